@@ -1,0 +1,145 @@
+"""CPU oracle for the polynomial-multiplication hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The library in
+``paper_1402_0264_gb300`` never imports it and shares no code with it.
+
+* ``polymul``/``coeff``/``evaluate``/``ntt_polymul``: thin ctypes wrappers over
+  ``polymul_oracle.c`` (the long-multiplication definition of Section 5 of
+  Haque, Moreno Maza, Xie, and a textbook radix-2 NTT used only as a faster
+  exact evaluator).
+* ``model``: the printed cost formulas of Section 5 and the Graham-Brent bound
+  of Section 2.4 (Theorem 1, Corollary 1), in fp64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "polymul_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libpolymul_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compiles the C oracle with gcc (plain -O2, no target-specific flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_polymul.argtypes = [_u32p, ctypes.c_int64, _u32p, ctypes.c_int64,
+                                           ctypes.c_uint32, _u32p]
+            lib.oracle_polymul.restype = ctypes.c_int
+            lib.oracle_coeff.argtypes = [_u32p, ctypes.c_int64, _u32p, ctypes.c_int64,
+                                         ctypes.c_uint32, ctypes.c_int64]
+            lib.oracle_coeff.restype = ctypes.c_uint32
+            lib.oracle_eval.argtypes = [_u32p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint32]
+            lib.oracle_eval.restype = ctypes.c_uint32
+            lib.oracle_powmod.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
+            lib.oracle_powmod.restype = ctypes.c_uint32
+            lib.oracle_ntt_polymul.argtypes = [_u32p, ctypes.c_int64, _u32p, ctypes.c_int64,
+                                               ctypes.c_uint32, ctypes.c_uint32, _u32p]
+            lib.oracle_ntt_polymul.restype = ctypes.c_int
+            for name in ("oracle_polymul_batch",):
+                fn = getattr(lib, name)
+                fn.argtypes = [ctypes.c_int64, _u32p, _i64p, _u32p, _i64p, _u32p, _i64p,
+                               ctypes.c_uint32]
+                fn.restype = ctypes.c_int
+            lib.oracle_ntt_polymul_batch.argtypes = [ctypes.c_int64, _u32p, _i64p, _u32p, _i64p,
+                                                     _u32p, _i64p, ctypes.c_uint32,
+                                                     ctypes.c_uint32]
+            lib.oracle_ntt_polymul_batch.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _u32(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.uint32))
+
+
+def _i64(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.int64))
+
+
+def _p(arr: np.ndarray, t):
+    return arr.ctypes.data_as(t)
+
+
+def polymul(a, b, p: int) -> np.ndarray:
+    """f = a*b mod p by the long-multiplication definition (Section 5)."""
+    a, b = _u32(a), _u32(b)
+    f = np.zeros(len(a) + len(b) - 1, dtype=np.uint32)
+    rc = _load().oracle_polymul(_p(a, _u32p), len(a), _p(b, _u32p), len(b), p, _p(f, _u32p))
+    if rc != 0:
+        raise ValueError("oracle_polymul: bad sizes")
+    return f
+
+
+def coeff(a, b, p: int, k: int) -> int:
+    """One coefficient f[k] of a*b mod p, by the definition."""
+    a, b = _u32(a), _u32(b)
+    return int(_load().oracle_coeff(_p(a, _u32p), len(a), _p(b, _u32p), len(b), p, k))
+
+
+def evaluate(poly, p: int, x: int) -> int:
+    """poly(x) mod p by Horner's rule."""
+    poly = _u32(poly)
+    return int(_load().oracle_eval(_p(poly, _u32p), len(poly), p, x))
+
+
+def powmod(base: int, e: int, p: int) -> int:
+    return int(_load().oracle_powmod(base, e, p))
+
+
+def ntt_polymul(a, b, p: int, g: int = 3) -> np.ndarray:
+    """a*b mod p through a textbook radix-2 NTT (exact; needs 2^k | p-1)."""
+    a, b = _u32(a), _u32(b)
+    f = np.zeros(len(a) + len(b) - 1, dtype=np.uint32)
+    rc = _load().oracle_ntt_polymul(_p(a, _u32p), len(a), _p(b, _u32p), len(b), p, g,
+                                    _p(f, _u32p))
+    if rc != 0:
+        raise ValueError(f"oracle_ntt_polymul failed ({rc})")
+    return f
+
+
+def polymul_batch(a_data, a_off, b_data, b_off, c_off, p: int) -> np.ndarray:
+    a_data, b_data = _u32(a_data), _u32(b_data)
+    a_off, b_off, c_off = _i64(a_off), _i64(b_off), _i64(c_off)
+    f = np.zeros(int(c_off[-1]), dtype=np.uint32)
+    rc = _load().oracle_polymul_batch(len(a_off) - 1, _p(a_data, _u32p), _p(a_off, _i64p),
+                                      _p(b_data, _u32p), _p(b_off, _i64p), _p(f, _u32p),
+                                      _p(c_off, _i64p), p)
+    if rc != 0:
+        raise ValueError("oracle_polymul_batch: bad sizes")
+    return f
+
+
+def ntt_polymul_batch(a_data, a_off, b_data, b_off, c_off, p: int, g: int = 3) -> np.ndarray:
+    a_data, b_data = _u32(a_data), _u32(b_data)
+    a_off, b_off, c_off = _i64(a_off), _i64(b_off), _i64(c_off)
+    f = np.zeros(int(c_off[-1]), dtype=np.uint32)
+    rc = _load().oracle_ntt_polymul_batch(len(a_off) - 1, _p(a_data, _u32p), _p(a_off, _i64p),
+                                          _p(b_data, _u32p), _p(b_off, _i64p), _p(f, _u32p),
+                                          _p(c_off, _i64p), p, g)
+    if rc != 0:
+        raise ValueError(f"oracle_ntt_polymul_batch failed ({rc})")
+    return f

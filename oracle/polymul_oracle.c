@@ -1,0 +1,163 @@
+/*
+ * CPU oracle for dense univariate polynomial multiplication modulo a
+ * word-size prime.  TEST INFRASTRUCTURE ONLY: the tests, the package's smoke
+ * check and the CPU-baseline leg of the bench call this; the library never
+ * does.  It shares no code, header or table with the CUDA path.
+ *
+ * What it computes (Haque, Moreno Maza, Xie, Section 5 "Polynomial
+ * multiplication"): for a, b over the field K = Z/pZ with n and m terms
+ * (deg a = n-1, deg b = m-1, terms counted "null or not" as in Section 3),
+ * f = a * b is the long-multiplication result
+ *     f[k] = sum_{i+j=k, 0<=i<n, 0<=j<m} a[i] * b[j]   (mod p),
+ * k = 0 .. n+m-2.  Every GPU path of this project (the s-blocked plain
+ * product of Algorithms 5-7, the batched form, the tensor-core form and the
+ * NTT form) must reproduce these residues exactly.
+ *
+ * Functions:
+ *   oracle_polymul            the definition above, one 128-bit running sum per k
+ *   oracle_coeff              one f[k] by the same definition (spot checks)
+ *   oracle_eval               Horner evaluation of a polynomial at a point
+ *   oracle_ntt_polymul        the same product through a textbook radix-2
+ *                             number-theoretic transform (Cooley-Tukey,
+ *                             bit-reversal permutation first); only a faster
+ *                             exact evaluator for sizes where the definition
+ *                             is too slow, pinned against the definition
+ *   oracle_powmod             modular exponentiation (square and multiply)
+ *
+ * Plain C, single threaded, unoptimised on purpose.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+
+typedef unsigned __int128 u128;
+
+static uint32_t mulmod(uint32_t x, uint32_t y, uint32_t p) {
+    return (uint32_t)(((uint64_t)x * (uint64_t)y) % p);
+}
+
+uint32_t oracle_powmod(uint32_t base, uint64_t e, uint32_t p) {
+    uint32_t r = 1 % p;
+    uint32_t b = base % p;
+    while (e) {
+        if (e & 1) r = mulmod(r, b, p);
+        b = mulmod(b, b, p);
+        e >>= 1;
+    }
+    return r;
+}
+
+/* f[k] for one k, by the definition (Section 5, long multiplication). */
+uint32_t oracle_coeff(const uint32_t *a, int64_t n, const uint32_t *b, int64_t m,
+                      uint32_t p, int64_t k) {
+    if (k < 0 || k > n + m - 2) return 0;
+    int64_t ilo = k - (m - 1) > 0 ? k - (m - 1) : 0;
+    int64_t ihi = k < n - 1 ? k : n - 1;
+    u128 acc = 0;
+    for (int64_t i = ilo; i <= ihi; ++i)
+        acc += (u128)a[i] * (u128)b[k - i];
+    return (uint32_t)(acc % p);
+}
+
+/* The full product f = a*b mod p; f has n+m-1 words.  Returns 0, or -1 on bad sizes. */
+int oracle_polymul(const uint32_t *a, int64_t n, const uint32_t *b, int64_t m,
+                   uint32_t p, uint32_t *f) {
+    if (n < 1 || m < 1 || p < 2) return -1;
+    for (int64_t k = 0; k <= n + m - 2; ++k)
+        f[k] = oracle_coeff(a, n, b, m, p, k);
+    return 0;
+}
+
+/* A batch in packed (CSR) form: pair i is a[a_off[i]..a_off[i+1]) etc. */
+int oracle_polymul_batch(int64_t batch, const uint32_t *a, const int64_t *a_off,
+                         const uint32_t *b, const int64_t *b_off,
+                         uint32_t *f, const int64_t *f_off, uint32_t p) {
+    for (int64_t i = 0; i < batch; ++i) {
+        int64_t n = a_off[i + 1] - a_off[i];
+        int64_t m = b_off[i + 1] - b_off[i];
+        if (f_off[i + 1] - f_off[i] != n + m - 1) return -1;
+        if (oracle_polymul(a + a_off[i], n, b + b_off[i], m, p, f + f_off[i]) != 0) return -1;
+    }
+    return 0;
+}
+
+/* Horner: poly(x) mod p for poly of len terms (index = degree). */
+uint32_t oracle_eval(const uint32_t *poly, int64_t len, uint32_t p, uint32_t x) {
+    uint64_t acc = 0;
+    for (int64_t i = len - 1; i >= 0; --i)
+        acc = ((acc * (uint64_t)(x % p)) + poly[i] % p) % p;
+    return (uint32_t)acc;
+}
+
+/* ---- textbook radix-2 NTT (in place, bit-reversal first, then log2 N stages) ---- */
+
+static void bit_reverse_permute(uint32_t *x, int64_t N) {
+    for (int64_t i = 1, j = 0; i < N; ++i) {
+        int64_t bit = N >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) { uint32_t t = x[i]; x[i] = x[j]; x[j] = t; }
+    }
+}
+
+/* y[k] = sum_j x[j] * w^(j*k) with w a primitive N-th root of unity mod p. */
+static void ntt_inplace(uint32_t *x, int64_t N, uint32_t w, uint32_t p) {
+    bit_reverse_permute(x, N);
+    for (int64_t len = 2; len <= N; len <<= 1) {
+        /* root of order len: w^(N/len) */
+        uint32_t wl = oracle_powmod(w, (uint64_t)(N / len), p);
+        for (int64_t start = 0; start < N; start += len) {
+            uint32_t t = 1;
+            for (int64_t j = 0; j < len / 2; ++j) {
+                uint32_t u = x[start + j];
+                uint32_t v = mulmod(x[start + j + len / 2], t, p);
+                x[start + j] = (uint32_t)(((uint64_t)u + v) % p);
+                x[start + j + len / 2] = (uint32_t)(((uint64_t)u + p - v) % p);
+                t = mulmod(t, wl, p);
+            }
+        }
+    }
+}
+
+/*
+ * f = a*b mod p through length-N transforms, N the least power of two
+ * >= n+m-1.  Needs 2^e | p-1 with N = 2^e and g a generator of (Z/p)^*.
+ * Returns 0, -1 on bad sizes, -2 if p-1 is not divisible by N, -3 on no memory.
+ */
+int oracle_ntt_polymul(const uint32_t *a, int64_t n, const uint32_t *b, int64_t m,
+                       uint32_t p, uint32_t g, uint32_t *f) {
+    if (n < 1 || m < 1 || p < 3) return -1;
+    int64_t L = n + m - 1, N = 1;
+    while (N < L) N <<= 1;
+    if ((uint64_t)(p - 1) % (uint64_t)N != 0) return -2;
+    uint32_t *x = (uint32_t *)calloc((size_t)N, sizeof(uint32_t));
+    uint32_t *y = (uint32_t *)calloc((size_t)N, sizeof(uint32_t));
+    if (!x || !y) { free(x); free(y); return -3; }
+    for (int64_t i = 0; i < n; ++i) x[i] = a[i] % p;
+    for (int64_t i = 0; i < m; ++i) y[i] = b[i] % p;
+    uint32_t w = oracle_powmod(g, (uint64_t)(p - 1) / (uint64_t)N, p);
+    ntt_inplace(x, N, w, p);
+    ntt_inplace(y, N, w, p);
+    for (int64_t i = 0; i < N; ++i) x[i] = mulmod(x[i], y[i], p);
+    /* inverse: transform with w^-1, then scale by N^-1 (Fermat inverses) */
+    uint32_t winv = oracle_powmod(w, (uint64_t)p - 2, p);
+    ntt_inplace(x, N, winv, p);
+    uint32_t ninv = oracle_powmod((uint32_t)(N % p), (uint64_t)p - 2, p);
+    for (int64_t i = 0; i < L; ++i) f[i] = mulmod(x[i], ninv, p);
+    free(x);
+    free(y);
+    return 0;
+}
+
+/* Batch through the transform, pair by pair (same CSR layout as above). */
+int oracle_ntt_polymul_batch(int64_t batch, const uint32_t *a, const int64_t *a_off,
+                             const uint32_t *b, const int64_t *b_off,
+                             uint32_t *f, const int64_t *f_off, uint32_t p, uint32_t g) {
+    for (int64_t i = 0; i < batch; ++i) {
+        int64_t n = a_off[i + 1] - a_off[i];
+        int64_t m = b_off[i + 1] - b_off[i];
+        if (f_off[i + 1] - f_off[i] != n + m - 1) return -1;
+        int rc = oracle_ntt_polymul(a + a_off[i], n, b + b_off[i], m, p, g, f + f_off[i]);
+        if (rc != 0) return rc;
+    }
+    return 0;
+}
