@@ -1,0 +1,175 @@
+/*
+ * polymul.h - C ABI of libpolymul.so: dense univariate polynomial
+ * multiplication modulo a word-size prime on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Haque, Moreno Maza, Xie, "A Many-core Machine Model for
+ * Designing Algorithms with Minimum Parallelism Overheads", Section 5, with
+ * the field and term conventions of Section 3): for a, b in K[X], K = Z/pZ,
+ * with n = deg a + 1 and m = deg b + 1 terms ("null or not"),
+ *
+ *     c[k] = sum_{i+j=k, 0<=i<n, 0<=j<m} a[i] * b[j]  mod p,   0 <= k < n+m-1.
+ *
+ * Conventions shared by every entry point
+ *   - Coefficients are uint32 in little-endian degree order (index = degree).
+ *     Inputs must be < p; outputs are canonical residues in [0, p).
+ *   - The output always has n+m-1 words; leading zeros are kept.
+ *   - Array arguments are DEVICE pointers (cudaMalloc'd or torch tensors),
+ *     owned by the caller.  The output must not overlap either input.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered and asynchronous: the return value
+ *     covers argument validation and the kernel launch only.  Errors raised
+ *     inside a kernel (a bounded wait that ran out) are recorded in a
+ *     per-device status word read by polymul_sync_status().
+ *   - The library owns a small per-device workspace (work lists, twiddle
+ *     tables, status word), grown on demand with cudaMalloc and freed by
+ *     polymul_release().  A call that would have to grow it while `stream`
+ *     is being captured into a CUDA graph returns PM_ERR_UNSUPPORTED: make
+ *     one uncaptured call of the same shape first.
+ *   - Thread safety: calls from several host threads are allowed; workspace
+ *     growth is serialised by a lock.  Calls that share a device and run
+ *     concurrently on different streams must not share output buffers.
+ */
+#ifndef POLYMUL_H
+#define POLYMUL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PM_OK = 0,
+    PM_ERR_INVALID_ARG = 1,  /* null pointer, bad degree, bad s or mode, overlap, bad offsets */
+    PM_ERR_RANGE = 2,        /* a size or modulus outside the supported range */
+    PM_ERR_UNSUPPORTED = 3,  /* valid request this path cannot serve (e.g. no 2^k root of unity) */
+    PM_ERR_NOMEM = 4,        /* workspace allocation failed */
+    PM_ERR_CUDA = 5,         /* a CUDA runtime call failed; see polymul_last_cuda_error() */
+    PM_ERR_TIMEOUT = 6,      /* a kernel's bounded wait ran out (reported by polymul_sync_status) */
+    PM_ERR_INTERNAL = 7
+} pm_status;
+
+/* Modes of polymul_batched. */
+#define PM_AUTO 0    /* tensor-core form where it applies, else the plain form */
+#define PM_PLAIN 1   /* s-blocked CUDA-core product */
+#define PM_TENSOR 2  /* bf16-limb Toeplitz product on the tcgen05 tensor cores */
+
+/* Largest supported modulus (exclusive) and degree (inclusive). */
+#define PM_MAX_P (1u << 30)
+#define PM_MAX_DEG ((int64_t)(1 << 30) - 2)
+
+/*
+ * polymul_plain - one product by the s-blocked long multiplication
+ * (Section 5, Algorithms 5-7: the multiplication phase forms s x s blocks of
+ * partial products per thread, the addition phase sums them; here both
+ * phases are fused in one kernel and the partial sums never leave the chip).
+ *
+ *   a, deg_a   device array of deg_a+1 coefficients (0 <= deg_a <= PM_MAX_DEG)
+ *   b, deg_b   device array of deg_b+1 coefficients (0 <= deg_b <= PM_MAX_DEG)
+ *   c          device array of deg_a+deg_b+1 words, written in full
+ *   p          modulus, 2 <= p < PM_MAX_P (need not be prime)
+ *   s          per-thread block parameter: 1, 2, 4, 8, 16, 32 or 64; 0 picks
+ *              the tuned value for this size (polymul_tune_plain) or a default
+ *   stream     cudaStream_t as void*
+ * Returns PM_OK, PM_ERR_INVALID_ARG or PM_ERR_CUDA.
+ */
+pm_status polymul_plain(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
+                        uint32_t *c, uint32_t p, int s, void *stream);
+
+/*
+ * polymul_ntt - one product through number-theoretic transforms: forward
+ * transforms of a and b zero-padded to N = 2^ceil(log2(n+m-1)), pointwise
+ * product, inverse transform, scaling by N^-1 mod p.  Exact, so the result
+ * equals polymul_plain's word for word.  (The paper has no transform path;
+ * this is the large-degree path of the same product.)
+ *
+ *   p must be prime with N | p-1 and g a generator of (Z/pZ)^*; pass g = 0
+ *   for p = 469762049 (7*2^26+1, generator 3).  N <= 2^26.
+ * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_UNSUPPORTED (N does not divide
+ * p-1, or no generator known), PM_ERR_NOMEM (twiddle tables) or PM_ERR_CUDA.
+ */
+pm_status polymul_ntt(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
+                      uint32_t *c, uint32_t p, uint32_t g, void *stream);
+
+/*
+ * polymul_batched - `batch` independent products in one persistent launch.
+ *
+ *   a_data, a_off  CSR: pair i's a is a_data[a_off[i] .. a_off[i+1]), at least one word
+ *   b_data, b_off  likewise for b
+ *   c_data, c_off  pair i's product goes to c_data[c_off[i] .. c_off[i+1]),
+ *                  which must hold exactly n_i + m_i - 1 words
+ *   The offset arrays (batch+1 int64 each) are DEVICE arrays, so the call can
+ *   be captured into a CUDA graph; they are validated on the device and a bad
+ *   layout sets PM_ERR_INVALID_ARG in the status word.
+ *   p              2 <= p < PM_MAX_P (PM_TENSOR: also see below)
+ *   mode           PM_PLAIN, PM_TENSOR or PM_AUTO
+ *   s              as for polymul_plain (PM_PLAIN / PM_AUTO); ignored by PM_TENSOR
+ *   max_deg        an upper bound on every degree in the batch (the host cannot
+ *                  read the device offsets); PM_TENSOR needs max_deg <= 4095
+ * PM_TENSOR computes the same residues on the tensor cores (bf16 limbs, fp32
+ * accumulation that stays exact below 2^24); it needs p < 2^29 and
+ * max_deg <= 4095, else returns PM_ERR_UNSUPPORTED.  PM_AUTO uses it when it
+ * applies.
+ * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_UNSUPPORTED, PM_ERR_NOMEM or PM_ERR_CUDA.
+ */
+pm_status polymul_batched(int64_t batch, const uint32_t *a_data, const int64_t *a_off,
+                          const uint32_t *b_data, const int64_t *b_off,
+                          uint32_t *c_data, const int64_t *c_off, uint32_t p,
+                          int mode, int s, int64_t max_deg, void *stream);
+
+/*
+ * polymul_model_predict - the cost model of the s-blocked product
+ * (Section 5 printed formulas; Theorem 1 and Corollary 1 of Section 2.4).
+ * Host-only; no GPU needed.
+ *
+ *   n, m   numbers of terms of a and b;  s, ell  block parameter and threads per block
+ *   U      cycles to move one word between global and local memory, in units of one
+ *          local operation (the machine parameter of Section 2.1)
+ *   P      number of streaming multiprocessors for Theorem 1
+ *   out    9 doubles: W_s, S_s, O_s, N_s, L_s, C_s, K (MulKer blocks),
+ *          T_thm = (N_s/P + L_s) C_s, T_cor = (N_s/K + L_s) C_s
+ * Returns PM_OK or PM_ERR_INVALID_ARG (n, m, s, ell < 1, s > m, U or P <= 0, out NULL).
+ */
+pm_status polymul_model_predict(int64_t n, int64_t m, int s, int ell, double U, double P,
+                                double *out);
+
+/*
+ * polymul_tune_plain - the autotuner: times polymul_plain for every s in
+ * {1,2,4,8,16,32,64} (CUDA events, `reps` launches each after one warm-up)
+ * on the caller's buffers, records the fastest s for this size class
+ * (log2 buckets of n and m, and p below or above 2^29) so that later s = 0
+ * calls use it, and returns the per-s milliseconds in times_ms[7]
+ * (may be NULL) and the chosen s in *best_s.  Synchronises `stream`.
+ * Returns what polymul_plain returns, or PM_ERR_CUDA.
+ */
+pm_status polymul_tune_plain(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
+                             uint32_t *c, uint32_t p, int reps, void *stream, int *best_s,
+                             float *times_ms);
+
+/* Returns the s that an s = 0 call of polymul_plain would use for these sizes. */
+int polymul_plain_default_s(int64_t deg_a, int64_t deg_b, uint32_t p);
+
+/*
+ * polymul_sync_status - synchronises `stream`, then returns and clears the
+ * device status word of the current device (PM_OK if no kernel reported an
+ * error since the last call).
+ */
+pm_status polymul_sync_status(void *stream);
+
+/* Frees every workspace the library holds on every device it used. */
+pm_status polymul_release(void);
+
+/* Static text for a status code. */
+const char *polymul_status_string(pm_status status);
+
+/* The last cudaError_t seen by a call that returned PM_ERR_CUDA (0 if none). */
+int polymul_last_cuda_error(void);
+
+/* Kernel launches made by this process so far (every entry point counts its own). */
+uint64_t polymul_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLYMUL_H */

@@ -1,0 +1,313 @@
+// C-ABI entry points of libpolymul: argument validation, the per-device
+// workspace, the device status word, the autotuner cache and the cost model.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "common.cuh"
+
+namespace pm {
+
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<int> g_last_cuda_error{0};
+static std::mutex g_ws_mutex;
+static DeviceWorkspace* g_ws[64] = {};
+
+pm_status cuda_fail(cudaError_t e) {
+    g_last_cuda_error.store((int)e);
+    return PM_ERR_CUDA;
+}
+
+void count_launches(uint64_t k) { g_launches.fetch_add(k); }
+
+bool is_capturing(void* stream) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+ModParams host_mod_params(uint32_t p, int kb) {
+    ModParams mp = {};
+    mp.p = p;
+    mp.c32 = (uint32_t)((1ull << 32) % p);
+    mp.mu = (uint64_t)(((unsigned __int128)1 << 64) / p);
+    // after fold2 the sum is at most 2^32 - 1 + c32^2 (see ModParams)
+    const unsigned __int128 bound = ((unsigned __int128)1 << 32) - 1 +
+                                    (unsigned __int128)mp.c32 * mp.c32;
+    const unsigned __int128 room = (((unsigned __int128)1 << 64) - 1) - bound;
+    const unsigned __int128 per_step = (unsigned __int128)kb * (uint64_t)(p - 1) * (uint64_t)(p - 1);
+    unsigned __int128 f = per_step ? room / per_step : 1000000;
+    if (f > 1000000) f = 1000000;
+    mp.fold_every = (int)(f < 1 ? 1 : f);
+    return mp;
+}
+
+DeviceWorkspace* workspace(void* stream, pm_status* err) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { *err = cuda_fail(e); return nullptr; }
+    if (dev < 0 || dev >= 64) { *err = PM_ERR_INTERNAL; return nullptr; }
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    if (g_ws[dev]) return g_ws[dev];
+    if (is_capturing(stream)) { *err = PM_ERR_UNSUPPORTED; return nullptr; }
+    DeviceWorkspace* w = new DeviceWorkspace();
+    w->device = dev;
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) { delete w; *err = cuda_fail(e); return nullptr; }
+    w->num_sms = prop.multiProcessorCount;
+    w->cc_major = prop.major;
+    w->cc_minor = prop.minor;
+    e = cudaMalloc((void**)&w->status, 256);
+    if (e != cudaSuccess) { delete w; *err = PM_ERR_NOMEM; return nullptr; }
+    e = cudaMemset(w->status, 0, 256);
+    if (e != cudaSuccess) { cudaFree(w->status); delete w; *err = cuda_fail(e); return nullptr; }
+    g_ws[dev] = w;
+    return w;
+}
+
+pm_status ensure_buffer(void** buf, size_t* have, size_t bytes, void* stream) {
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    if (*have >= bytes && *buf) return PM_OK;
+    if (is_capturing(stream)) return PM_ERR_UNSUPPORTED;
+    size_t want = *have ? *have : 1;
+    while (want < bytes) want *= 2;
+    void* nb = nullptr;
+    if (cudaMalloc(&nb, want) != cudaSuccess) {
+        cudaGetLastError();
+        return PM_ERR_NOMEM;
+    }
+    if (*buf) {
+        // the old buffer may still be read by work queued on any stream
+        cudaDeviceSynchronize();
+        cudaFree(*buf);
+    }
+    *buf = nb;
+    *have = want;
+    return PM_OK;
+}
+
+// ---- autotuner cache: (device, log2 n, log2 m, p >= 2^29) -> s ----
+static std::mutex g_tune_mutex;
+static std::map<std::tuple<int, int, int, int>, int> g_tuned;
+
+static int ilog2(int64_t x) {
+    int r = 0;
+    while (x > 1) { x >>= 1; ++r; }
+    return r;
+}
+
+static std::tuple<int, int, int, int> tune_key(int64_t n, int64_t m, uint32_t p) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (n < m) std::swap(n, m);
+    return std::make_tuple(dev, ilog2(n), ilog2(m), p >= (1u << 29) ? 1 : 0);
+}
+
+static int default_s(int64_t n, int64_t m, uint32_t p) {
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tuned.find(tune_key(n, m, p));
+        if (it != g_tuned.end()) return it->second;
+    }
+    const int64_t mn = n < m ? n : m;
+    if (mn >= 1024) return 8;
+    if (mn >= 64) return 4;
+    return 2;
+}
+
+static bool valid_s(int s) {
+    return s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32 || s == 64;
+}
+
+static bool overlaps(const void* x, int64_t xw, const void* y, int64_t yw) {
+    const uintptr_t x0 = (uintptr_t)x, x1 = x0 + 4 * (uintptr_t)xw;
+    const uintptr_t y0 = (uintptr_t)y, y1 = y0 + 4 * (uintptr_t)yw;
+    return x0 < y1 && y0 < x1;
+}
+
+static pm_status check_pair(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64_t deg_b,
+                            const uint32_t* c, uint32_t p) {
+    if (!a || !b || !c) return PM_ERR_INVALID_ARG;
+    if (deg_a < 0 || deg_b < 0 || deg_a > PM_MAX_DEG || deg_b > PM_MAX_DEG) return PM_ERR_INVALID_ARG;
+    if (p < 2 || p >= PM_MAX_P) return PM_ERR_RANGE;
+    const int64_t L = deg_a + deg_b + 1;
+    if (overlaps(c, L, a, deg_a + 1) || overlaps(c, L, b, deg_b + 1)) return PM_ERR_INVALID_ARG;
+    return PM_OK;
+}
+
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+pm_status polymul_plain(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64_t deg_b,
+                        uint32_t* c, uint32_t p, int s, void* stream) {
+    pm_status rc = check_pair(a, deg_a, b, deg_b, c, p);
+    if (rc != PM_OK) return rc;
+    if (s != 0 && !valid_s(s)) return PM_ERR_INVALID_ARG;
+    if (s == 0) s = default_s(deg_a + 1, deg_b + 1, p);
+    DeviceWorkspace* ws = workspace(stream, &rc);
+    if (!ws) return rc;
+    return launch_plain(a, deg_a + 1, b, deg_b + 1, c, p, s, (cudaStream_t)stream, ws);
+}
+
+pm_status polymul_ntt(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64_t deg_b,
+                      uint32_t* c, uint32_t p, uint32_t g, void* stream) {
+    pm_status rc = check_pair(a, deg_a, b, deg_b, c, p);
+    if (rc != PM_OK) return rc;
+    DeviceWorkspace* ws = workspace(stream, &rc);
+    if (!ws) return rc;
+    return launch_ntt(a, deg_a + 1, b, deg_b + 1, c, p, g, (cudaStream_t)stream, ws);
+}
+
+pm_status polymul_batched(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
+                          const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
+                          const int64_t* c_off, uint32_t p, int mode, int s, int64_t max_deg,
+                          void* stream) {
+    if (batch < 0 || batch > (int64_t)(1 << 24)) return PM_ERR_INVALID_ARG;
+    if (batch == 0) return PM_OK;
+    if (!a_data || !a_off || !b_data || !b_off || !c_data || !c_off) return PM_ERR_INVALID_ARG;
+    if (max_deg < 0 || max_deg > PM_MAX_DEG) return PM_ERR_INVALID_ARG;
+    if (p < 2 || p >= PM_MAX_P) return PM_ERR_RANGE;
+    if (mode != PM_AUTO && mode != PM_PLAIN && mode != PM_TENSOR) return PM_ERR_INVALID_ARG;
+    if (s != 0 && !valid_s(s)) return PM_ERR_INVALID_ARG;
+    if (c_data == a_data || c_data == b_data) return PM_ERR_INVALID_ARG;
+    const bool tensor_ok = p < (1u << 29) && max_deg <= 4095;
+    if (mode == PM_TENSOR && !tensor_ok) return PM_ERR_UNSUPPORTED;
+    pm_status rc = PM_OK;
+    DeviceWorkspace* ws = workspace(stream, &rc);
+    if (!ws) return rc;
+    if (mode == PM_TENSOR || (mode == PM_AUTO && tensor_ok)) {
+        rc = launch_batched_tensor(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg,
+                                   (cudaStream_t)stream, ws);
+        if (rc != PM_ERR_UNSUPPORTED || mode == PM_TENSOR) return rc;
+    }
+    if (s == 0) s = default_s(max_deg + 1, max_deg + 1, p) > 4 ? 4 : default_s(max_deg + 1, max_deg + 1, p);
+    return launch_batched_plain(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, s, max_deg,
+                                (cudaStream_t)stream, ws);
+}
+
+pm_status polymul_model_predict(int64_t n, int64_t m, int s, int ell, double U, double P,
+                                double* out) {
+    if (!out || n < 1 || m < 1 || s < 1 || ell < 1 || s > m || !(U > 0) || !(P > 0))
+        return PM_ERR_INVALID_ARG;
+    // Section 5 (printed formulas) with Theorem 1 and Corollary 1 (Section 2.4).
+    const double nn = (double)n, mm = (double)m, ss = (double)s, l = (double)ell;
+    const double y = nn + ss - 1.0;                      // row length of M
+    const double W = (2.0 * mm - 0.5) * y;
+    const double S = 2.0 * ss * ss + ss * std::log2(mm / ss) - ss;
+    const double O = y * (5.0 * mm * ss + 2.0 * mm - 3.0 * ss * ss) * U / (ss * ss * l);
+    const double N = y * (2.0 * mm - ss) / (ss * ss * l);
+    const double L = std::log2(mm / ss) + 1.0;
+    const double C = ss * (2.0 * ss - 1.0) + 2.0 * U * (ss + 1.0);
+    const double K = (mm / ss) * y / (ss * l);          // MulKer thread-blocks
+    out[0] = W; out[1] = S; out[2] = O; out[3] = N; out[4] = L; out[5] = C; out[6] = K;
+    out[7] = (N / P + L) * C;
+    out[8] = (N / K + L) * C;
+    return PM_OK;
+}
+
+pm_status polymul_tune_plain(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64_t deg_b,
+                             uint32_t* c, uint32_t p, int reps, void* stream, int* best_s,
+                             float* times_ms) {
+    static const int cand[7] = {1, 2, 4, 8, 16, 32, 64};
+    if (!best_s || reps < 1) return PM_ERR_INVALID_ARG;
+    pm_status rc = check_pair(a, deg_a, b, deg_b, c, p);
+    if (rc != PM_OK) return rc;
+    if (is_capturing(stream)) return PM_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(cudaGetLastError()); }
+    float best = 1e30f;
+    int bs = 0;
+    for (int i = 0; i < 7; ++i) {
+        const int s = cand[i];
+        if (s > deg_a + 1 && s > deg_b + 1) { if (times_ms) times_ms[i] = -1.0f; continue; }
+        rc = polymul_plain(a, deg_a, b, deg_b, c, p, s, stream);
+        if (rc != PM_OK) break;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps && rc == PM_OK; ++r) rc = polymul_plain(a, deg_a, b, deg_b, c, p, s, stream);
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { rc = cuda_fail(e); break; }
+        if (rc != PM_OK) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        if (times_ms) times_ms[i] = ms;
+        if (ms < best) { best = ms; bs = s; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != PM_OK) return rc;
+    *best_s = bs;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[tune_key(deg_a + 1, deg_b + 1, p)] = bs;
+    return PM_OK;
+}
+
+int polymul_plain_default_s(int64_t deg_a, int64_t deg_b, uint32_t p) {
+    return default_s(deg_a + 1, deg_b + 1, p);
+}
+
+pm_status polymul_sync_status(void* stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    pm_status rc = PM_OK;
+    DeviceWorkspace* ws = workspace(stream, &rc);
+    if (!ws) return rc;
+    int v = 0;
+    e = cudaMemcpy(&v, ws->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (v != 0) {
+        e = cudaMemset(ws->status, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return (pm_status)v;
+}
+
+pm_status polymul_release(void) {
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < 64; ++d) {
+        DeviceWorkspace* w = g_ws[d];
+        if (!w) continue;
+        cudaSetDevice(d);
+        cudaDeviceSynchronize();
+        cudaFree(w->status);
+        if (w->batch_ws) cudaFree(w->batch_ws);
+        if (w->ntt_ws) cudaFree(w->ntt_ws);
+        delete w;
+        g_ws[d] = nullptr;
+    }
+    cudaSetDevice(cur);
+    return PM_OK;
+}
+
+const char* polymul_status_string(pm_status status) {
+    switch (status) {
+        case PM_OK: return "ok";
+        case PM_ERR_INVALID_ARG: return "invalid argument";
+        case PM_ERR_RANGE: return "size or modulus out of range";
+        case PM_ERR_UNSUPPORTED: return "unsupported for this path";
+        case PM_ERR_NOMEM: return "workspace allocation failed";
+        case PM_ERR_CUDA: return "CUDA runtime error";
+        case PM_ERR_TIMEOUT: return "bounded wait ran out";
+        case PM_ERR_INTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+int polymul_last_cuda_error(void) { return g_last_cuda_error.load(); }
+
+uint64_t polymul_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

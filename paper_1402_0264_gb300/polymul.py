@@ -1,0 +1,182 @@
+"""Python binding of libpolymul.so (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/polymul.h with
+device pointers taken from torch CUDA tensors and the current torch stream.
+There is no CPU path: tensors must live on a CUDA device and the library
+must have been built (``python -m paper_1402_0264_gb300.build``); otherwise
+these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpolymul.so")
+
+P_DEFAULT = 469762049
+PM_AUTO, PM_PLAIN, PM_TENSOR = 0, 1, 2
+S_CANDIDATES = (1, 2, 4, 8, 16, 32, 64)
+
+STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_RANGE", 3: "PM_ERR_UNSUPPORTED",
+          4: "PM_ERR_NOMEM", 5: "PM_ERR_CUDA", 6: "PM_ERR_TIMEOUT", 7: "PM_ERR_INTERNAL"}
+
+
+class PolymulError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_u32p = ctypes.c_void_p
+_i64 = ctypes.c_int64
+
+
+def _declare(lib):
+    V, I64, U32, INT, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int, ctypes.c_double
+    sig = {
+        "polymul_plain": ([V, I64, V, I64, V, U32, INT, V], INT),
+        "polymul_ntt": ([V, I64, V, I64, V, U32, U32, V], INT),
+        "polymul_batched": ([I64, V, V, V, V, V, V, U32, INT, INT, I64, V], INT),
+        "polymul_model_predict": ([I64, I64, INT, INT, D, D, ctypes.POINTER(D)], INT),
+        "polymul_tune_plain": ([V, I64, V, I64, V, U32, INT, V, ctypes.POINTER(INT),
+                                ctypes.POINTER(ctypes.c_float)], INT),
+        "polymul_plain_default_s": ([I64, I64, U32], INT),
+        "polymul_sync_status": ([V], INT),
+        "polymul_release": ([], INT),
+        "polymul_status_string": ([INT], ctypes.c_char_p),
+        "polymul_last_cuda_error": ([], INT),
+        "polymul_launch_count": ([], ctypes.c_uint64),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libpolymul.so not built (expected at {LIB_PATH}); run "
+                                   "python -m paper_1402_0264_gb300.build")
+            _lib = _declare(ctypes.CDLL(LIB_PATH))
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise PolymulError(rc, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_words(t, name: str):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (no CPU path)")
+    if t.element_size() != 4 or not t.is_contiguous() or t.dim() != 1:
+        raise TypeError(f"{name} must be a contiguous 1-D tensor of 32-bit words")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_i64(t, name: str):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.int64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous int64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _alloc(n: int, like):
+    torch = _torch()
+    return torch.empty(n, dtype=torch.uint32, device=like.device)
+
+
+def plain(a, b, p: int = P_DEFAULT, s: int = 0, out=None, stream=None):
+    """c = a*b mod p by the s-blocked product (s = 0: tuned/default)."""
+    L = a.numel() + b.numel() - 1
+    out = _alloc(L, a) if out is None else out
+    if out.numel() != L:
+        raise ValueError("out must hold len(a) + len(b) - 1 words")
+    _check(lib().polymul_plain(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"), b.numel() - 1,
+                               _dev_words(out, "out"), p, s, _stream_ptr(stream)), "polymul_plain")
+    return out
+
+
+def ntt(a, b, p: int = P_DEFAULT, g: int = 0, out=None, stream=None):
+    """c = a*b mod p through number-theoretic transforms."""
+    L = a.numel() + b.numel() - 1
+    out = _alloc(L, a) if out is None else out
+    if out.numel() != L:
+        raise ValueError("out must hold len(a) + len(b) - 1 words")
+    _check(lib().polymul_ntt(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"), b.numel() - 1,
+                             _dev_words(out, "out"), p, g, _stream_ptr(stream)), "polymul_ntt")
+    return out
+
+
+def batched(a_data, a_off, b_data, b_off, c_off, max_deg: int, p: int = P_DEFAULT,
+            mode: int = PM_PLAIN, s: int = 0, out=None, total: int | None = None, stream=None):
+    """Products of a CSR batch; `total` = c_off[-1] (read from the device if None)."""
+    batch = a_off.numel() - 1
+    if total is None:
+        total = int(c_off[-1].item())
+    out = _alloc(total, a_data) if out is None else out
+    _check(lib().polymul_batched(batch, _dev_words(a_data, "a_data"), _dev_i64(a_off, "a_off"),
+                                 _dev_words(b_data, "b_data"), _dev_i64(b_off, "b_off"),
+                                 _dev_words(out, "out"), _dev_i64(c_off, "c_off"), p, mode, s,
+                                 max_deg, _stream_ptr(stream)), "polymul_batched")
+    return out
+
+
+def model_predict(n: int, m: int, s: int, ell: int, U: float, P: float) -> dict:
+    """Section 5 cost formulas with Theorem 1 / Corollary 1 (host code, no GPU)."""
+    out = (ctypes.c_double * 9)()
+    _check(lib().polymul_model_predict(n, m, s, ell, U, P, out), "polymul_model_predict")
+    keys = ("W", "S", "O", "N", "L", "C", "K", "T_thm", "T_cor")
+    return dict(zip(keys, list(out)))
+
+
+def tune_plain(a, b, p: int = P_DEFAULT, reps: int = 5, out=None, stream=None):
+    """Times every s, records the best for this size class; returns (best_s, {s: ms})."""
+    L = a.numel() + b.numel() - 1
+    out = _alloc(L, a) if out is None else out
+    best = ctypes.c_int(0)
+    times = (ctypes.c_float * 7)()
+    _check(lib().polymul_tune_plain(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"),
+                                    b.numel() - 1, _dev_words(out, "out"), p, reps,
+                                    _stream_ptr(stream), ctypes.byref(best), times),
+           "polymul_tune_plain")
+    return best.value, {s: t for s, t in zip(S_CANDIDATES, list(times)) if t >= 0}
+
+
+def default_s(deg_a: int, deg_b: int, p: int = P_DEFAULT) -> int:
+    return lib().polymul_plain_default_s(deg_a, deg_b, p)
+
+
+def sync_status(stream=None) -> int:
+    """Synchronises the stream; returns and clears the device status word."""
+    return lib().polymul_sync_status(_stream_ptr(stream))
+
+
+def launch_count() -> int:
+    return int(lib().polymul_launch_count())
+
+
+def release():
+    _check(lib().polymul_release(), "polymul_release")

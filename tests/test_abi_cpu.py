@@ -1,0 +1,98 @@
+"""CPU checks of the C ABI: the library loads, exports every declared symbol,
+validates arguments before touching the GPU, and its host cost model matches
+the oracle's fp64 model.  No kernel runs here."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from oracle import model as omodel
+from paper_1402_0264_gb300 import build as pbuild
+from paper_1402_0264_gb300 import polymul as pm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pbuild.build()
+    return pm.lib()
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(polymul_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert lib.polymul_status_string(code)
+    assert lib.polymul_status_string(0) == b"ok"
+
+
+NULL = ctypes.c_void_p(0)
+FAKE = ctypes.c_void_p(0x10000)       # never dereferenced: validation fails first
+FAKE2 = ctypes.c_void_p(0x20000000)
+
+
+def test_plain_validation_happens_on_host(lib):
+    f = lib.polymul_plain
+    assert f(NULL, 3, FAKE, 3, FAKE2, pm.P_DEFAULT, 0, NULL) == 1      # null input
+    assert f(FAKE, -1, FAKE, 3, FAKE2, pm.P_DEFAULT, 0, NULL) == 1     # negative degree
+    assert f(FAKE, 3, FAKE2, 2**30, FAKE2, pm.P_DEFAULT, 0, NULL) == 1  # degree too large
+    assert f(FAKE, 3, FAKE2, 3, ctypes.c_void_p(0x30000000), 1, 0, NULL) == 2    # p < 2
+    assert f(FAKE, 3, FAKE2, 3, ctypes.c_void_p(0x30000000), 2**30, 0, NULL) == 2  # p too large
+    assert f(FAKE, 3, FAKE2, 3, ctypes.c_void_p(0x30000000), 7, 3, NULL) == 1    # s not a power of two
+    assert f(FAKE, 3, FAKE2, 3, ctypes.c_void_p(0x30000000), 7, 128, NULL) == 1  # s too large
+    # c overlapping a: [0x10000, +7 words) vs [0x10008, ...)
+    assert f(FAKE, 3, FAKE2, 3, ctypes.c_void_p(0x10008), 7, 0, NULL) == 1
+
+
+def test_batched_validation_happens_on_host(lib):
+    f = lib.polymul_batched
+    assert f(0, NULL, NULL, NULL, NULL, NULL, NULL, 7, 1, 0, 10, NULL) == 0   # empty batch: no-op
+    assert f(-1, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 7, 1, 0, 10, NULL) == 1
+    assert f(4, FAKE, NULL, FAKE, FAKE, FAKE2, FAKE, 7, 1, 0, 10, NULL) == 1
+    assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 7, 9, 0, 10, NULL) == 1  # bad mode
+    assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 7, 1, 5, 10, NULL) == 1  # bad s
+    assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 1, 1, 0, 10, NULL) == 2  # bad p
+    assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 7, 1, 0, -1, NULL) == 1  # bad max_deg
+    # tensor mode outside its exactness bounds
+    assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 2**29 + 11, 2, 0, 100, NULL) == 3
+    assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 7, 2, 0, 4096, NULL) == 3
+
+
+def test_ntt_validation_happens_on_host(lib):
+    f = lib.polymul_ntt
+    assert f(NULL, 3, FAKE, 3, FAKE2, pm.P_DEFAULT, 0, NULL) == 1
+    assert f(FAKE, 3, FAKE2, 3, ctypes.c_void_p(0x30000000), 2**30 + 1, 0, NULL) == 2
+
+
+@pytest.mark.parametrize("n,m", [(4000, 4000), (8000, 1000), (16384, 16384), (1024, 1024)])
+@pytest.mark.parametrize("s", [1, 2, 4, 8, 16, 32, 64])
+@pytest.mark.parametrize("U", [1.5, 22.0, 400.0])
+def test_model_matches_oracle(lib, n, m, s, U):
+    got = pm.model_predict(n, m, s, 256, U, 152.0)
+    want = omodel.predict(n, m, s, 256, U, 152.0)
+    for k, v in want.items():
+        assert abs(got[k] - v) <= 1e-12 * abs(v), k
+
+
+def test_model_rejects_bad_args(lib):
+    with pytest.raises(pm.PolymulError):
+        pm.model_predict(100, 4, 8, 256, 10.0, 152.0)   # s > m
+    with pytest.raises(pm.PolymulError):
+        pm.model_predict(100, 100, 4, 256, 0.0, 152.0)  # U <= 0

@@ -1,0 +1,93 @@
+"""Parity of the batched persistent form with the CPU oracle (every word)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_0264_gb300 import inputs
+from paper_1402_0264_gb300 import polymul as pm
+from tests.gpuhelp import assert_equal, dev, dev64, host
+
+pytestmark = pytest.mark.gpu
+P = inputs.P_DEFAULT
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_0264_gb300 import build
+    build.build()
+
+
+def run_batch(packed, max_deg, p=P, mode=pm.PM_PLAIN, s=0):
+    a_data, a_off, b_data, b_off, c_off = packed
+    out = pm.batched(dev(a_data), dev64(a_off), dev(b_data), dev64(b_off), dev64(c_off),
+                     max_deg=max_deg, p=p, mode=mode, s=s, total=int(c_off[-1]))
+    assert pm.sync_status() == 0
+    return host(out)
+
+
+def test_batched_workload_full():
+    """4096 pairs, degrees log-uniform in [16, 2048]."""
+    packed = inputs.workload_batched()
+    want = oracle.polymul_batch(*packed[:4], packed[4], P)
+    assert_equal(run_batch(packed, 2048), want, "4096 pairs")
+
+
+@pytest.mark.parametrize("s", [1, 2, 4, 8, 16, 32, 64])
+def test_ragged_small_batch(s):
+    da = np.array([0, 1, 5, 1000, 7, 0, 2047, 300, 64, 4096], np.int64)
+    db = np.array([0, 3, 5, 17, 2000, 999, 2047, 1, 64, 33], np.int64)
+    packed = inputs.packed_batch(da, db, 77)
+    want = oracle.polymul_batch(*packed[:4], packed[4], P)
+    assert_equal(run_batch(packed, 4096, s=s), want, f"s={s}")
+
+
+def test_batch_of_one_and_unsorted_path():
+    packed = inputs.packed_batch(np.array([5000]), np.array([3000]), 5)
+    assert_equal(run_batch(packed, 5000), oracle.polymul_batch(*packed[:4], packed[4], P))
+    # more pairs than the shared-memory sort holds: natural order path
+    da = inputs.log_uniform_degrees(20000, 1, 41, 9, 1) - 1
+    db = inputs.log_uniform_degrees(20000, 1, 41, 9, 2) - 1
+    packed = inputs.packed_batch(da, db, 9)
+    assert_equal(run_batch(packed, 40), oracle.polymul_batch(*packed[:4], packed[4], P))
+
+
+def test_bad_offsets_report_invalid_arg():
+    import torch
+    da = np.array([10, 20, 30], np.int64)
+    packed = list(inputs.packed_batch(da, da, 3))
+    c_off = packed[4].copy()
+    c_off[2] += 1  # pair 1 gets a wrong output length
+    out = torch.full((int(c_off[-1]),), 7, dtype=torch.uint32, device="cuda")
+    pm.batched(dev(packed[0]), dev64(packed[1]), dev(packed[2]), dev64(packed[3]), dev64(c_off),
+               max_deg=30, out=out, total=int(c_off[-1]))
+    assert pm.sync_status() == 1  # PM_ERR_INVALID_ARG from the device-side check
+    assert (host(out) == 7).all()  # nothing written
+    # degrees above max_deg are refused the same way
+    packed = inputs.packed_batch(da, da, 3)
+    pm.batched(dev(packed[0]), dev64(packed[1]), dev(packed[2]), dev64(packed[3]),
+               dev64(packed[4]), max_deg=20, total=int(packed[4][-1]))
+    assert pm.sync_status() == 1
+    assert pm.sync_status() == 0  # cleared
+
+
+def test_graph_capture_replay():
+    import torch
+    packed = inputs.workload_batched(batch=512)
+    want = oracle.polymul_batch(*packed[:4], packed[4], P)
+    a_data, a_off, b_data, b_off, c_off = [dev(x) if x.dtype == np.uint32 else dev64(x) for x in packed]
+    out = torch.zeros(int(packed[4][-1]), dtype=torch.uint32, device="cuda")
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        pm.batched(a_data, a_off, b_data, b_off, c_off, max_deg=2048, out=out, total=out.numel(), stream=st)
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    out.zero_()
+    with torch.cuda.graph(g, stream=st):
+        pm.batched(a_data, a_off, b_data, b_off, c_off, max_deg=2048, out=out, total=out.numel(), stream=st)
+    for _ in range(3):
+        out.zero_()
+        g.replay()
+        assert_equal(host(out), want, "graph replay")
