@@ -1,0 +1,473 @@
+#!/usr/bin/env python3
+"""Benchmark: modular coefficient MACs/s of dense polynomial multiplication
+mod p = 469762049 on one GB300, bit-exact against the CPU oracle.
+
+Headline step: one product of a degree-16383 pair (n = m = 16384, so
+n*m = 2^28 modular multiply-adds) by the s-blocked plain kernel at the tuned
+s.  Each timed step is bracketed by CUDA events on the launching stream and
+preceded by a 256 MiB write that flushes the 129 MB L2 (outside the events).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-rows]
+
+Prints one JSON line.  With N > 1 (torchrun) every rank runs its own replica
+of the step (the product does not shard here) and rank 0 reports the job
+total over the slowest rank's time.  `rows` holds the other measured paths:
+the s sweep with the cost model's predictions, the batched form, and (where
+built) the tensor-core and transform forms.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1402_0264_gb300 import inputs  # noqa: E402
+
+P = inputs.P_DEFAULT
+METRIC = "modular coefficient MACs/s (n*m per product), bit-exact vs oracle"
+UNIT = "MAC/s"
+N_SINGLE = 16384
+MACS_SINGLE = N_SINGLE * N_SINGLE
+WORKLOAD = "plain polymul mod p=469762049, one pair of degree 16383, uint32 coefficients uniform in [0,p)"
+FLUSH_BYTES = 256 << 20
+SMS = 152
+IMAD_PER_CLK_SM = 32      # acc64 += u32*u32 (IMAD.WIDE.U32) issue rate measured on GB300: one per modular MAC
+SM_MAX_MHZ = 2070.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            pk = json.load(fh)
+        return pk, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+def alu_peak_macs(mhz=SM_MAX_MHZ):
+    """Plain-path ceiling: one mad.wide.u32 per modular MAC, 64 per SM per clock."""
+    return SMS * IMAD_PER_CLK_SM * mhz * 1e6
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1402_0264_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, src: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except OSError:
+        return None
+    ent = t.get(kernel)
+    if not ent or ent.get("source_sha") != source_hash(src):
+        return None
+    return ent.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index  # nvidia-smi --id value (UUID of the CUDA device)
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        mhz = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ---------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    """The oracle on the host cores.  Each step is the full product when K+W full
+    products fit in about two minutes, else the product of the leading n' terms
+    of both operands (a bounded sample of the same workload, n'^2 MACs)."""
+    if rank != 0:
+        return 0
+    import oracle
+    a, b = inputs.workload_single()
+    t0 = time.perf_counter()
+    oracle.polymul(a, b, P)  # build, load and time one full product
+    t_full = time.perf_counter() - t0
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    nn = N_SINGLE
+    if t_full > budget:
+        nn = max(256, int(N_SINGLE * math.sqrt(budget / t_full)))
+    a_s, b_s = a[:nn], b[:nn]
+    for _ in range(args.warmup):
+        oracle.polymul(a_s, b_s, P)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.polymul(a_s, b_s, P)
+    dt = time.perf_counter() - t0
+    value = nn * nn * args.steps / dt
+    sample = (f"{args.steps} full products of the degree-16383 pair" if nn == N_SINGLE else
+              f"{args.steps} products of the leading {nn} terms of both operands of the degree-16383 pair")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N_SINGLE, "m": N_SINGLE, "p": P},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample + " (single-thread C schoolbook, 128-bit accumulation)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1402_0264_gb300 import build as pbuild
+    from paper_1402_0264_gb300 import polymul as pm
+
+    if not os.path.exists(pm.LIB_PATH):
+        pbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def flush():
+        flush_buf.zero_()
+
+    a_np, b_np = inputs.workload_single()
+    a = torch.from_numpy(a_np).to(dev)
+    b = torch.from_numpy(b_np).to(dev)
+    c = torch.empty(2 * N_SINGLE - 1, dtype=torch.uint32, device=dev)
+
+    # autotune s on this size (the tuner records it; s = 0 calls then use it)
+    if args.s:
+        s, tune_ms = args.s, {}
+    else:
+        s, tune_ms = pm.tune_plain(a, b, reps=10, out=c)
+
+    # warm-up + parity of the warmed result
+    for _ in range(args.warmup):
+        pm.plain(a, b, s=s, out=c)
+    torch.cuda.synchronize()
+    if rank == 0:
+        import oracle
+        want = oracle.polymul(a_np, b_np, P)
+        got = c.cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), "bench: result differs from the oracle"
+    assert pm.sync_status() == 0
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    launches0 = pm.launch_count()
+    try:
+        smi_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        smi_id = str(local)
+    sampler = ClockSampler(smi_id)
+    with sampler:
+        barrier(world)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for i in range(K):
+            flush()
+            starts[i].record(stream)
+            pm.plain(a, b, s=s, out=c)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - w0
+    launches = pm.launch_count() - launches0
+    clocks = sampler.summary()
+    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+    total_ms = max_over_ranks(sum(step_ms), world)
+    value = world * MACS_SINGLE * K / (total_ms * 1e-3)
+    ms_per_step = total_ms / K
+
+    # end to end through the C ABI from pinned host buffers (H2D, product, D2H each step)
+    a_h = torch.from_numpy(a_np).pin_memory()
+    b_h = torch.from_numpy(b_np).pin_memory()
+    c_h = torch.empty(2 * N_SINGLE - 1, dtype=torch.uint32).pin_memory()
+    e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush()
+        e_starts[i].record(stream)
+        a.copy_(a_h, non_blocking=True)
+        b.copy_(b_h, non_blocking=True)
+        pm.plain(a, b, s=s, out=c)
+        c_h.copy_(c, non_blocking=True)
+        e_ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in zip(e_starts, e_ends)), world)
+    if rank == 0:
+        import oracle
+        assert np.array_equal(c_h.numpy().view(np.uint32), oracle.polymul(a_np, b_np, P))
+
+    if rank != 0:
+        return 0
+
+    pk, pk_kind = peaks()
+    kern_name = f"plain_pair_kernel<{s}>"
+    achieved = MACS_SINGLE / (ms_per_step * 1e-3)
+    peak = alu_peak_macs()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "products_per_s": value / MACS_SINGLE,
+        "config": {"workload": WORKLOAD, "n": N_SINGLE, "m": N_SINGLE, "p": P, "s": s,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "MAC/s",
+                     "frac": achieved / peak,
+                     "peak_basis": "152 SMs x 32 IMAD.WIDE.U32 (64-bit accumulate) per clk per SM, measured, x 2070 MHz max SM clock; one per modular MAC",
+                     "frac_at_sampled_clock": (achieved / alu_peak_macs(clocks["sm_mhz"])
+                                               if clocks.get("sm_mhz") else None),
+                     "kernel": kern_name,
+                     "traffic": traffic_for(f"plain_pair_kernel<{s}>", "plain.cu")},
+        "e2e": {"value": world * MACS_SINGLE * K / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(a_h.numel() * 4 + b_h.numel() * 4),
+                "d2h_bytes_per_step": int(c_h.numel() * 4)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+        "peaks_source": pk_kind,
+        "tune_ms": {str(k): v for k, v in tune_ms.items()},
+    }
+    if world == 1 and not args.no_rows:
+        line["rows"] = measure_rows(pm, torch, dev, flush, clocks, pk)
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a_np, b_np)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def median_ms(fn, reps, flush, stream):
+    import torch
+    ts = []
+    for _ in range(reps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def measure_rows(pm, torch, dev, flush, clocks, pk):
+    import oracle
+    from oracle import model as omodel  # noqa: F401  (the library's own model is used below)
+    stream = torch.cuda.current_stream()
+    rows = {}
+    mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+
+    # --- s sweep on the degree-16383 pair with the cost model beside each point ---
+    a_np, b_np = inputs.workload_single()
+    a = torch.from_numpy(a_np).to(dev)
+    b = torch.from_numpy(b_np).to(dev)
+    c = torch.empty(2 * N_SINGLE - 1, dtype=torch.uint32, device=dev)
+    ell = 256
+    U = 256.0 * SM_MAX_MHZ * 1e6 * SMS / (pk["hbm_gbs"] * 1e9)  # word move / local op (see DESIGN)
+    unit_s = ell / (IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6)         # one local op of a whole block
+    sweep = []
+    for s in pm.S_CANDIDATES:
+        ms = median_ms(lambda: pm.plain(a, b, s=s, out=c), 20, flush, stream)
+        pred = pm.model_predict(N_SINGLE, N_SINGLE, s, ell, U, float(SMS))
+        sweep.append({"s": s, "ms": ms, "macs_per_s": MACS_SINGLE / (ms * 1e-3),
+                      "alu_frac": MACS_SINGLE / (ms * 1e-3) / alu_peak_macs(),
+                      "model_T_thm_s": pred["T_thm"] * unit_s, "model_T_cor_s": pred["T_cor"] * unit_s,
+                      "model_W": pred["W"], "model_O": pred["O"]})
+    rows["plain_s_sweep"] = {"workload": "degree-16383 pair", "ell": ell, "U": U, "P": SMS,
+                             "time_unit_s": unit_s, "points": sweep,
+                             "best_measured_s": min(sweep, key=lambda r: r["ms"])["s"],
+                             "best_thm_s": min(sweep, key=lambda r: r["model_T_thm_s"])["s"],
+                             "best_cor_s": min(sweep, key=lambda r: r["model_T_cor_s"])["s"]}
+
+    # --- degree-1023 pair (latency bound) ---
+    a0, b0 = inputs.workload_small()
+    da0, db0 = torch.from_numpy(a0).to(dev), torch.from_numpy(b0).to(dev)
+    c0 = torch.empty(2047, dtype=torch.uint32, device=dev)
+    s0 = pm.tune_plain(da0, db0, reps=10, out=c0)[0]
+    ms0 = median_ms(lambda: pm.plain(da0, db0, s=s0, out=c0), 50, flush, stream)
+    assert np.array_equal(c0.cpu().numpy().view(np.uint32), oracle.polymul(a0, b0, P))
+    rows["plain_small"] = {"workload": "degree-1023 pair", "s": s0, "ms": ms0,
+                           "macs_per_s": 1024 * 1024 / (ms0 * 1e-3)}
+
+    # --- batched: 4096 pairs, degrees log-uniform in [16, 2048], one graph launch ---
+    packed = inputs.workload_batched()
+    a_data, a_off, b_data, b_off, c_off = packed
+    macs = int(((a_off[1:] - a_off[:-1]) * (b_off[1:] - b_off[:-1])).sum())
+    ta = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in packed]
+    outb = torch.empty(int(c_off[-1]), dtype=torch.uint32, device=dev)
+    best = None
+    for s in (2, 4, 8):
+        run = lambda s=s: pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_PLAIN,
+                                     s=s, out=outb, total=outb.numel())
+        run()
+        ms = median_ms(run, 10, flush, stream)
+        if best is None or ms < best[1]:
+            best = (s, ms)
+    s_b = best[0]
+    g = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream()
+    with torch.cuda.stream(gs):
+        pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_PLAIN, s=s_b, out=outb,
+                   total=outb.numel(), stream=gs)
+        gs.synchronize()
+        with torch.cuda.graph(g, stream=gs):
+            pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_PLAIN, s=s_b,
+                       out=outb, total=outb.numel(), stream=gs)
+    ms_g = median_ms(g.replay, 20, flush, stream)
+    want = oracle.polymul_batch(a_data, a_off, b_data, b_off, c_off, P)
+    assert np.array_equal(outb.cpu().numpy().view(np.uint32), want)
+    rows["batched_plain"] = {"workload": "4096 pairs, degrees log-uniform in [16,2048]", "s": s_b,
+                             "macs": macs, "ms_graph": ms_g, "ms_direct": best[1],
+                             "macs_per_s": macs / (ms_g * 1e-3), "products_per_s": 4096 / (ms_g * 1e-3),
+                             "alu_frac": macs / (ms_g * 1e-3) / alu_peak_macs()}
+    return rows
+
+
+def cpu_baseline(a_np, b_np):
+    import oracle
+    oracle.polymul(a_np[:8], b_np[:8], P)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.polymul(a_np, b_np, P)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt > 10.0 or reps >= 100:
+            break
+    return {"value": MACS_SINGLE * reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full products of the degree-16383 pair, single-thread C schoolbook "
+                      f"with 128-bit accumulation ({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-rows", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--s", type=int, default=0, help="fix the block parameter (skip the tuner)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -31,18 +31,31 @@ bool is_capturing(void* stream) {
 }
 
 ModParams host_mod_params(uint32_t p, int kb) {
+    typedef unsigned __int128 u128;
     ModParams mp = {};
     mp.p = p;
     mp.c32 = (uint32_t)((1ull << 32) % p);
-    mp.mu = (uint64_t)(((unsigned __int128)1 << 64) / p);
-    // after fold2 the sum is at most 2^32 - 1 + c32^2 (see ModParams)
-    const unsigned __int128 bound = ((unsigned __int128)1 << 32) - 1 +
-                                    (unsigned __int128)mp.c32 * mp.c32;
-    const unsigned __int128 room = (((unsigned __int128)1 << 64) - 1) - bound;
-    const unsigned __int128 per_step = (unsigned __int128)kb * (uint64_t)(p - 1) * (uint64_t)(p - 1);
-    unsigned __int128 f = per_step ? room / per_step : 1000000;
-    if (f > 1000000) f = 1000000;
-    mp.fold_every = (int)(f < 1 ? 1 : f);
+    mp.mu = (uint64_t)(((u128)1 << 64) / p);
+    const u128 top = ((u128)1 << 64) - 1;
+    const u128 per_step = (u128)kb * (uint64_t)(p - 1) * (uint64_t)(p - 1);
+    // bounds after one and after two applications of the fold map
+    const u128 b1 = (((u128)1 << 32) - 1) * ((u128)mp.c32 + 1);
+    const u128 b2 = ((u128)1 << 32) - 1 + (u128)mp.c32 * mp.c32;
+    auto steps = [&](u128 bound) -> int64_t {
+        if (per_step == 0) return 1000000;
+        if (bound + per_step > top) return 0;
+        u128 f = (top - bound) / per_step;
+        return f > 1000000 ? 1000000 : (int64_t)f;
+    };
+    const int64_t f1 = steps(b1), f2 = steps(b2);
+    // cost per sub-step: a single fold is half the work of a double one
+    if (f1 >= 1 && 2 * f1 >= f2) {
+        mp.fold_every = (int)f1;
+        mp.fold_twice = 0;
+    } else {
+        mp.fold_every = (int)(f2 < 1 ? 1 : f2);
+        mp.fold_twice = 1;
+    }
     return mp;
 }
 
@@ -66,15 +79,27 @@ DeviceWorkspace* workspace(void* stream, pm_status* err) {
     if (e != cudaSuccess) { delete w; *err = PM_ERR_NOMEM; return nullptr; }
     e = cudaMemset(w->status, 0, 256);
     if (e != cudaSuccess) { cudaFree(w->status); delete w; *err = cuda_fail(e); return nullptr; }
+    w->streams = new std::map<cudaStream_t, StreamScratch*>();
     g_ws[dev] = w;
     return w;
 }
 
-pm_status ensure_buffer(void** buf, size_t* have, size_t bytes, void* stream) {
+pm_status stream_scratch(DeviceWorkspace* ws, cudaStream_t st, StreamScratch** out) {
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    auto* mp = static_cast<std::map<cudaStream_t, StreamScratch*>*>(ws->streams);
+    auto it = mp->find(st);
+    if (it != mp->end()) { *out = it->second; return PM_OK; }
+    StreamScratch* sc = new StreamScratch();
+    (*mp)[st] = sc;
+    *out = sc;
+    return PM_OK;
+}
+
+pm_status ensure_scratch(void** buf, size_t* have, size_t bytes, cudaStream_t st, bool zero) {
     std::lock_guard<std::mutex> lock(g_ws_mutex);
     if (*have >= bytes && *buf) return PM_OK;
-    if (is_capturing(stream)) return PM_ERR_UNSUPPORTED;
-    size_t want = *have ? *have : 1;
+    if (is_capturing(st)) return PM_ERR_UNSUPPORTED;
+    size_t want = 4096;
     while (want < bytes) want *= 2;
     void* nb = nullptr;
     if (cudaMalloc(&nb, want) != cudaSuccess) {
@@ -82,9 +107,13 @@ pm_status ensure_buffer(void** buf, size_t* have, size_t bytes, void* stream) {
         return PM_ERR_NOMEM;
     }
     if (*buf) {
-        // the old buffer may still be read by work queued on any stream
-        cudaDeviceSynchronize();
+        // work queued earlier on this stream may still use the old buffer
+        cudaStreamSynchronize(st);
         cudaFree(*buf);
+    }
+    if (zero) {
+        cudaError_t e = cudaMemsetAsync(nb, 0, want, st);
+        if (e != cudaSuccess) { cudaFree(nb); return cuda_fail(e); }
     }
     *buf = nb;
     *have = want;
@@ -283,8 +312,17 @@ pm_status polymul_release(void) {
         cudaSetDevice(d);
         cudaDeviceSynchronize();
         cudaFree(w->status);
-        if (w->batch_ws) cudaFree(w->batch_ws);
-        if (w->ntt_ws) cudaFree(w->ntt_ws);
+        if (w->twiddles) cudaFree(w->twiddles);
+        auto* mp = static_cast<std::map<cudaStream_t, StreamScratch*>*>(w->streams);
+        for (auto& kv : *mp) {
+            StreamScratch* sc = kv.second;
+            if (sc->sk) cudaFree(sc->sk);
+            if (sc->plan) cudaFree(sc->plan);
+            if (sc->tc) cudaFree(sc->tc);
+            if (sc->ntt) cudaFree(sc->ntt);
+            delete sc;
+        }
+        delete mp;
         delete w;
         g_ws[d] = nullptr;
     }

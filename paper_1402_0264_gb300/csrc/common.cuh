@@ -16,9 +16,11 @@ namespace pm {
 // Section 3; it does not say how sums are formed): products a*b < p^2 are
 // summed unreduced in 64 bits.  Every `fold_every` sub-steps the sum is
 // folded twice with x -> (x mod 2^32) + floor(x / 2^32) * (2^32 mod p), which
-// keeps it congruent mod p and brings it below fold_bound, so that
-// fold_bound + fold_every * KB * (p-1)^2 < 2^64 always holds (KB products per
-// accumulator per sub-step).  The final value is reduced with Barrett's method
+// keeps it congruent mod p.  One application leaves at most
+// (2^32-1)(c+1) with c = 2^32 mod p, two leave at most 2^32-1+c^2; the host
+// picks one or two applications and the largest fold_every such that
+// bound + fold_every * KB * (p-1)^2 < 2^64 (KB products per accumulator per
+// sub-step), whichever costs fewer instructions per product.  The final value is reduced with Barrett's method
 // (P. Barrett, "Implementing the RSA public key encryption algorithm on a
 // standard digital signal processor", CRYPTO 1986): q = floor(x * mu / 2^64)
 // with mu = floor(2^64 / p) underestimates floor(x / p) by at most one, so
@@ -29,13 +31,26 @@ struct ModParams {
     uint32_t c32;       // 2^32 mod p
     uint64_t mu;        // floor(2^64 / p)
     int fold_every;     // sub-steps (of KB products) between two folds
-    int pad_;
+    int fold_twice;     // 1: a fold applies the map twice, 0: once
 };
 
+#ifndef PM_MACFORM
+#define PM_MACFORM 0  // 0: C++ product + add, 1: mad.wide.u32, 2: mad.lo.cc/madc.hi pair
+#endif
+// acc + x*y with a 32x32->64 product
 __device__ __forceinline__ uint64_t mad_wide(uint32_t x, uint32_t y, uint64_t acc) {
+#if PM_MACFORM == 1
     uint64_t r;
     asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(r) : "r"(x), "r"(y), "l"(acc));
     return r;
+#elif PM_MACFORM == 2
+    uint32_t lo = (uint32_t)acc, hi = (uint32_t)(acc >> 32);
+    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\tmadc.hi.u32 %1, %2, %3, %1;"
+        : "+r"(lo), "+r"(hi) : "r"(x), "r"(y));
+    return ((uint64_t)hi << 32) | lo;
+#else
+    return acc + (uint64_t)x * (uint64_t)y;
+#endif
 }
 
 __device__ __forceinline__ uint64_t fold_once(uint64_t x, uint32_t c32) {
@@ -57,25 +72,40 @@ __device__ __forceinline__ uint32_t barrett(uint64_t x, uint32_t p, uint64_t mu)
 // ---------------------------------------------------------------------------
 ModParams host_mod_params(uint32_t p, int kb);
 
-// Per-device workspace owned by the library.
+// Scratch owned by the library for one (device, stream): calls on one stream
+// are ordered, so they can share it; calls on different streams never do.
+struct StreamScratch {
+    void* sk = nullptr;            // partial-sum slots and counters of the plain kernels
+    size_t sk_bytes = 0;
+    void* plan = nullptr;          // position prefix of polymul_batched
+    size_t plan_bytes = 0;
+    void* tc = nullptr;            // tensor-core path scratch
+    size_t tc_bytes = 0;
+    void* ntt = nullptr;           // transform buffers
+    size_t ntt_bytes = 0;
+};
+
+// Per-device state owned by the library.
 struct DeviceWorkspace {
     int device = -1;
     int num_sms = 0;
     int cc_major = 0, cc_minor = 0;
     int* status = nullptr;          // device status word (pm_status), zero = PM_OK
-    void* batch_ws = nullptr;       // work list of polymul_batched
-    size_t batch_ws_bytes = 0;
-    void* ntt_ws = nullptr;         // twiddle tables and transform scratch
-    size_t ntt_ws_bytes = 0;
-    uint32_t ntt_p = 0, ntt_g = 0;  // modulus/generator the tables were built for
-    int ntt_logN = -1;
+    void* twiddles = nullptr;       // transform twiddle tables (read-only, shared by streams)
+    size_t twiddle_bytes = 0;
+    uint32_t tw_p = 0, tw_g = 0;    // modulus/generator the tables were built for
+    int tw_logn = -1;
+    void* streams = nullptr;        // map cudaStream_t -> StreamScratch* (api.cu)
 };
 
 // Returns the workspace of the current device, creating it on first use.
 // Never allocates while `stream` is capturing (returns null then).
 DeviceWorkspace* workspace(void* stream, pm_status* err);
-// Grows *buf to at least `bytes` (cudaMalloc; refused during capture).
-pm_status ensure_buffer(void** buf, size_t* have, size_t bytes, void* stream);
+// The scratch of (ws's device, stream), created on first use.
+pm_status stream_scratch(DeviceWorkspace* ws, cudaStream_t st, StreamScratch** out);
+// Grows *buf to at least `bytes` (cudaMalloc; refused during capture); when it
+// allocates and `zero` is set, clears the new buffer on `st`.
+pm_status ensure_scratch(void** buf, size_t* have, size_t bytes, cudaStream_t st, bool zero);
 
 pm_status cuda_fail(cudaError_t e);
 void count_launches(uint64_t k);
@@ -83,7 +113,7 @@ bool is_capturing(void* stream);
 
 // Kernel launchers (one translation unit each).
 pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c,
-                       uint32_t p, int s, cudaStream_t st, const DeviceWorkspace* ws);
+                       uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws);
 pm_status launch_batched_plain(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                const int64_t* c_off, uint32_t p, int s, int64_t max_deg,

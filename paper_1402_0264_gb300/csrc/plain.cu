@@ -2,58 +2,81 @@
 //
 // Paper -> this file
 //   Algorithm 6 (MulKer): a thread-block copies s coefficients of b and a
-//   window of a to local memory and each thread forms s results, each a
-//   length-s dot product, written to the auxiliary array M.
-//   Algorithm 7 (AddKer): log2(m/s)+1 kernel launches add the rows of M
-//   pairwise into f.
-// Here one kernel does both phases.  Lane l of a warp owns the s consecutive
-// outputs d0 + s*l + e (e < s) of a tile of 32*s outputs.  Per sub-step it
-// takes KB = min(s, 8) coefficients of b (a broadcast shared-memory read) and
-// forms the s x KB block of products a[d-j] b[j] from a register window of
-// s+KB-1 coefficients of a that slides by KB per sub-step; the row sums that
-// the paper writes to M stay in 64-bit registers (the multiplication phase),
-// and the addition phase is the running sum itself plus two reductions: the 8
-// warps of a CTA split the b-range of the tile and add their partial sums in
-// shared memory, and up to 8 CTAs of a thread-block cluster split it further
-// and add through distributed shared memory.  M never reaches global memory.
+//   window of a to local memory; each thread forms s results, each a
+//   length-s dot product, and writes them to the auxiliary array M.
+//   Algorithm 7 (AddKer): log2(m/s)+1 launches add the rows of M pairwise.
+// Here both phases run in one persistent kernel and M never reaches global
+// memory.  Lane l of a warp owns the s consecutive outputs d0 + s*l + e
+// (e < s) of a tile of 32*s outputs.  Per sub-step it takes KB = min(s, 8)
+// coefficients of b (one broadcast shared-memory read) and forms the s x KB
+// block of products a[d-j] b[j] from a register window of s+KB-1 coefficients
+// of a, kept as a ring of KB-word groups that slides by one group per
+// sub-step (so no register moves).  Row sums stay in 64-bit registers: that is
+// the multiplication phase with the first levels of the addition phase fused
+// into it.  The 8 warps of a CTA split the b-range of a tile and add their
+// partial sums in shared memory.
+//
+// Work distribution.  The paper's kernels are grids of independent blocks;
+// with one CTA per output tile the largest tiles finish last and the SMs idle
+// (a tail of about one tile).  Instead every tile t of every pair is cut into
+// len(t) "positions", one per coefficient of b that meets the tile (len(t) =
+// min(m, (t+1)T) - max(0, tT - n + 1) for T = 32 s outputs per tile, with a
+// the longer operand), and the G positions of the whole job are split into P
+// equal contiguous ranges, one per persistent CTA.  A tile covered by one CTA
+// is written directly; a tile cut by CTA boundaries gets one partial sum per
+// CTA in a scratch slot, and the CTA that arrives last at the tile's counter
+// adds them and writes the output (the counter is reset by that CTA, so the
+// scratch is clean for the next call).  No CTA ever waits for another.
 //
 // Staging (the paper's copy to local memory): per chunk of at most
 // CHUNK_MAX coefficients of b, the chunk and the a-window it meets
 // (32*s + chunk - 1 coefficients, zero outside [0, n)) are copied with
-// coalesced loads into shared memory; a is stored with one pad word every
-// 32 (s <= 32) or 64 words so that the 32 lanes' window loads, s words
-// apart, hit 32 different banks.
-#include <cooperative_groups.h>
-
+// coalesced loads into shared memory.  The a-window is stored in 16-byte
+// chunks with one pad chunk after every 8, so that the 32 lanes' 128-bit
+// window loads (s words apart) fall in distinct banks for s = 4..32.
 #include <algorithm>
 
 #include "common.cuh"
 
-namespace cg = cooperative_groups;
-
 namespace pm {
 
-constexpr int WB = 8;              // warps per CTA, all on one output tile
-constexpr int NT = 32 * WB;        // threads per CTA
-constexpr int CHUNK_MAX = 2048;    // b coefficients staged per chunk
+#ifndef PM_WB
+#define PM_WB 8
+#endif
+constexpr int WB = PM_WB;        // warps per CTA, all on one output tile
+constexpr int NT = 32 * WB;      // threads per CTA
+constexpr int CHUNK_MAX = 2048;  // b coefficients staged per chunk (two chunks in flight)
+constexpr int FRONT = 8;         // a-window words before index 0 (read by the last prefetch)
+
+// Build-time tuning knobs (defaults chosen by measurement on GB300).
+#ifndef PM_MINB
+#define PM_MINB 0                // __launch_bounds__ minimum blocks per SM (0: none)
+#endif
+#if PM_MINB > 0
+#define PM_BOUNDS __launch_bounds__(32 * PM_WB, PM_MINB)
+#else
+#define PM_BOUNDS __launch_bounds__(32 * PM_WB)
+#endif
 
 template <int S>
 struct Cfg {
-    static constexpr int KB = S < 8 ? S : 8;     // b coefficients per sub-step
-    static constexpr int WIN = S + KB - 1;        // a-window registers per lane
-    static constexpr int TD = 32 * S;             // outputs per tile
-    static constexpr int PADSH = S > 32 ? 6 : 5;  // one pad word per 2^PADSH words
-    static constexpr int A_WORDS = TD + CHUNK_MAX - 1 + ((TD + CHUNK_MAX) >> PADSH) + 4;
-    static constexpr int PSTRIDE = TD + 32;       // row of the per-warp partial sums
-    static constexpr size_t SMEM =
-        sizeof(uint32_t) * (size_t)(((A_WORDS + 3) & ~3) + CHUNK_MAX + WB * PSTRIDE + TD);
+    static constexpr int KB = S < 8 ? S : 8;                   // b coefficients per sub-step
+    static constexpr int NGW = (S + KB - 1 + KB - 1) / KB;     // window groups of KB words
+    static constexpr int R = NGW + 1;                          // ring slots (one prefetched)
+    static constexpr int TD = 32 * S;                          // outputs per tile
+    static constexpr int A_LOGICAL = FRONT + TD + CHUNK_MAX + 8;
+    static constexpr int A_CHUNKS = (A_LOGICAL + 3) / 4;
+    static constexpr int A_WORDS = 4 * (A_CHUNKS + A_CHUNKS / 8 + 2);
+    static constexpr int PSTRIDE = TD + 32;                    // row of per-warp partial sums
+    static constexpr int BUF_WORDS = A_WORDS + CHUNK_MAX;       // one staging buffer
+    static constexpr size_t SMEM = 4 * (size_t)(2 * BUF_WORDS + WB * PSTRIDE + TD);
 };
 
-__device__ __forceinline__ int padded(int i, int sh) { return i + (i >> sh); }
+// word offset of logical a-window word i (16-byte chunks, a pad chunk every 8)
+__device__ __forceinline__ int a_phys(int i) { return 4 * ((i >> 2) + (i >> 5)) + (i & 3); }
 
 struct Smem {
-    uint32_t* sA;
-    uint32_t* sB;
+    uint32_t* buf;   // two staging buffers: a-window (A_WORDS) then b-chunk (CHUNK_MAX)
     uint32_t* part;
     uint32_t* red;
 };
@@ -62,77 +85,160 @@ template <int S>
 __device__ __forceinline__ Smem carve(uint32_t* base) {
     using C = Cfg<S>;
     Smem s;
-    s.sA = base;
-    s.sB = s.sA + ((C::A_WORDS + 3) & ~3);
-    s.part = s.sB + CHUNK_MAX;
+    s.buf = base;
+    s.part = s.buf + 2 * C::BUF_WORDS;
     s.red = s.part + WB * C::PSTRIDE;
     return s;
 }
 
+// 4-byte asynchronous global->shared copy; with valid == false it writes a zero
+// and reads nothing (src-size 0), src is then only a placeholder address.
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Chunk `ci` of the b-range [jb0, jb1): start, length and padded length CL
+// (a multiple of KB).  Warp w takes sub-steps [first, first + count) of the
+// CL / KB sub-steps, the counts differing by at most one.
+struct ChunkDims {
+    int jc, clen, CL;
+};
+template <int KB>
+__device__ __forceinline__ ChunkDims chunk_dims(int jb0, int jb1, int ci) {
+    ChunkDims c;
+    c.jc = jb0 + ci * CHUNK_MAX;
+    c.clen = min(CHUNK_MAX, jb1 - c.jc);
+    c.CL = (c.clen + KB - 1) / KB * KB;
+    return c;
+}
+
+// Issues the copies of one chunk: b[jc .. jc+clen) (zeros up to CL) and the
+// a-window a[d0-(jc+CL-1) .. d0+TD-jc) (zeros outside [0, n)).
+template <int S>
+__device__ __forceinline__ void stage_chunk(const uint32_t* __restrict__ a, int n,
+                                            const uint32_t* __restrict__ b, int d0,
+                                            const ChunkDims& ch, uint32_t* buf) {
+    using C = Cfg<S>;
+    uint32_t* sA = buf;
+    uint32_t* sB = buf + C::A_WORDS;
+    for (int i = threadIdx.x; i < ch.CL; i += NT) {
+        const bool v = i < ch.clen;
+        cp_async4(sB + i, b + (v ? ch.jc + i : 0), v);
+    }
+    const int abase = d0 - (ch.jc + ch.CL - 1);
+    const int alen = C::TD + ch.CL - 1;
+    for (int i = threadIdx.x; i < alen; i += NT) {
+        const int ai = abase + i;
+        const bool v = ai >= 0 && ai < n;
+        cp_async4(sA + a_phys(FRONT + i), a + (v ? ai : 0), v);
+    }
+    cp_async_commit();
+}
+
+// One group of KB consecutive a-window words starting at window index `base`.
+template <int S>
+__device__ __forceinline__ void load_group(const uint32_t* sA, int base, uint32_t (&g)[Cfg<S>::KB]) {
+    constexpr int KB = Cfg<S>::KB;
+    const int li = FRONT + base;
+    if constexpr (KB >= 4) {  // li is a multiple of 4 here
+#pragma unroll
+        for (int h = 0; h < KB / 4; ++h) {
+            const int j = (li >> 2) + h;
+            const uint4 v = *reinterpret_cast<const uint4*>(sA + 4 * (j + (j >> 3)));
+            g[4 * h] = v.x; g[4 * h + 1] = v.y; g[4 * h + 2] = v.z; g[4 * h + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < KB; ++t) g[t] = sA[a_phys(li + t)];
+    }
+}
+
 // Multiplication phase of one tile: acc[e] = sum over j in [jb0, jb1) of
-// a[d - j] * b[j] for d = d0 + S*lane + e, with a taken as zero outside
-// [0, n).  Values are congruent mod p and below 2^64 (see ModParams).
+// a[d - j] b[j] for d = d0 + S*lane + e, a taken as zero outside [0, n).
+// Values stay congruent mod p and below 2^64 (see ModParams).
 template <int S>
 __device__ __forceinline__ void tile_accumulate(const uint32_t* __restrict__ a, int n,
                                                 const uint32_t* __restrict__ b, int d0, int jb0,
                                                 int jb1, const ModParams& mp, const Smem& sm,
                                                 uint64_t (&acc)[S]) {
     using C = Cfg<S>;
-    constexpr int KB = C::KB;
+    constexpr int KB = C::KB, NGW = C::NGW, R = C::R;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int e = 0; e < S; ++e) acc[e] = 0;
     int fold_ctr = 0;
-    for (int jc = jb0; jc < jb1; jc += CHUNK_MAX) {
-        const int clen = min(CHUNK_MAX, jb1 - jc);
-        const int wlen = (((clen + WB - 1) / WB) + 7) & ~7;  // per warp, multiple of 8
-        const int CL = wlen * WB;                             // padded chunk, <= CHUNK_MAX
-        __syncthreads();                                      // previous chunk fully consumed
-        for (int i = threadIdx.x; i < CL; i += NT) sm.sB[i] = (i < clen) ? __ldg(b + jc + i) : 0u;
-        const int abase = d0 - (jc + CL - 1);
-        const int alen = C::TD + CL - 1;
-        for (int i = threadIdx.x; i < alen; i += NT) {
-            const int ai = abase + i;
-            sm.sA[padded(i, C::PADSH)] = (ai >= 0 && ai < n) ? __ldg(a + ai) : 0u;
+    const int nchunks = (jb1 - jb0 + CHUNK_MAX - 1) / CHUNK_MAX;
+    stage_chunk<S>(a, n, b, d0, chunk_dims<KB>(jb0, jb1, 0), sm.buf);
+    for (int ci = 0; ci < nchunks; ++ci) {
+        const ChunkDims ch = chunk_dims<KB>(jb0, jb1, ci);
+        if (ci + 1 < nchunks) {  // the next chunk streams in while this one is used
+            stage_chunk<S>(a, n, b, d0, chunk_dims<KB>(jb0, jb1, ci + 1),
+                           sm.buf + ((ci + 1) & 1) * C::BUF_WORDS);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-
-        const int r0 = warp * wlen;
-        int base = S * lane + CL - KB - r0;  // sA index of window slot 0 at sub-step r0
-        uint32_t w[C::WIN];
+        const uint32_t* sA = sm.buf + (ci & 1) * C::BUF_WORDS;
+        const uint32_t* sB = sA + C::A_WORDS;
+        const int CL = ch.CL;
+        const int tot = CL / KB, qw = tot / WB, rw = tot % WB;
+        const int nsub = qw + (warp < rw ? 1 : 0);
+        const int r0 = KB * (warp * qw + min(warp, rw));
+        int base = S * lane + CL - KB - r0;  // window index of group 0 at the current sub-step
+        uint32_t ring[R][KB];
 #pragma unroll
-        for (int t = 0; t < C::WIN; ++t) w[t] = sm.sA[padded(base + t, C::PADSH)];
-        for (int q = 0; q < wlen; q += KB) {
-            uint32_t bv[KB];
-            if constexpr (KB >= 4) {
+        for (int g = 0; g < NGW; ++g) load_group<S>(sA, base + g * KB, ring[(R - g) % R]);
+        const uint32_t* bp = sB + r0;
+        for (int q0 = 0; q0 < nsub; q0 += R) {
 #pragma unroll
-                for (int k4 = 0; k4 < KB; k4 += 4) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(sm.sB + r0 + q + k4);
-                    bv[k4] = v.x; bv[k4 + 1] = v.y; bv[k4 + 2] = v.z; bv[k4 + 3] = v.w;
+            for (int u = 0; u < R; ++u) {
+                if (q0 + u < nsub) {
+                    load_group<S>(sA, base - KB, ring[(u + 1) % R]);  // group 0 of the next sub-step
+                    uint32_t bv[KB];
+                    if constexpr (KB >= 4) {
+#pragma unroll
+                        for (int k4 = 0; k4 < KB; k4 += 4) {
+                            const uint4 v = *reinterpret_cast<const uint4*>(bp + k4);
+                            bv[k4] = v.x; bv[k4 + 1] = v.y; bv[k4 + 2] = v.z; bv[k4 + 3] = v.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < KB; ++k) bv[k] = bp[k];
+                    }
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) {
+#pragma unroll
+                        for (int e = 0; e < S; ++e) {
+                            const int t = e - k + KB - 1;  // window word of a[d - j]
+                            acc[e] = mad_wide(ring[(u - t / KB + R) % R][t % KB], bv[k], acc[e]);
+                        }
+                    }
+                    if (++fold_ctr == mp.fold_every) {
+                        fold_ctr = 0;
+                        if (mp.fold_twice) {
+#pragma unroll
+                            for (int e = 0; e < S; ++e) acc[e] = fold2(acc[e], mp.c32);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < S; ++e) acc[e] = fold_once(acc[e], mp.c32);
+                        }
+                    }
+                    base -= KB;
+                    bp += KB;
                 }
-            } else {
-#pragma unroll
-                for (int k = 0; k < KB; ++k) bv[k] = sm.sB[r0 + q + k];
-            }
-#pragma unroll
-            for (int k = 0; k < KB; ++k) {
-#pragma unroll
-                for (int e = 0; e < S; ++e) acc[e] = mad_wide(w[e - k + KB - 1], bv[k], acc[e]);
-            }
-            if (++fold_ctr == mp.fold_every) {
-                fold_ctr = 0;
-#pragma unroll
-                for (int e = 0; e < S; ++e) acc[e] = fold2(acc[e], mp.c32);
-            }
-            if (q + KB < wlen) {  // slide the window by KB towards lower a indices
-#pragma unroll
-                for (int t = C::WIN - 1; t >= KB; --t) w[t] = w[t - KB];
-                base -= KB;
-#pragma unroll
-                for (int t = 0; t < KB; ++t) w[t] = sm.sA[padded(base + t, C::PADSH)];
             }
         }
+        __syncthreads();  // this buffer is refilled two chunks later
     }
 }
 
@@ -146,8 +252,7 @@ __device__ __forceinline__ void cta_reduce(uint64_t (&acc)[S], const ModParams& 
     const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int e = 0; e < S; ++e)
-        sm.part[warp * C::PSTRIDE + (S + 1) * lane + e] =
-            barrett(fold2(acc[e], mp.c32), mp.p, mp.mu);
+        sm.part[warp * C::PSTRIDE + (S + 1) * lane + e] = barrett(fold2(acc[e], mp.c32), mp.p, mp.mu);
     __syncthreads();
     for (int o = threadIdx.x; o < C::TD; o += NT) {
         uint64_t s = 0;
@@ -158,80 +263,169 @@ __device__ __forceinline__ void cta_reduce(uint64_t (&acc)[S], const ModParams& 
     __syncthreads();
 }
 
-// Heavy-first tile order: the middle of the product has the longest sums.
-__device__ __forceinline__ int heavy_first(int i, int ntiles) {
-    const int mid = (ntiles - 1) / 2;
-    const int k = (i + 1) / 2;
-    return (i & 1) ? mid + k : mid - k;
+// ---- positions: len(t) and its prefix sum in closed form (n >= m >= 1) ----
+__host__ __device__ __forceinline__ int64_t ntiles_of(int64_t n, int64_t m, int64_t td) {
+    return (n + m - 1 + td - 1) / td;
 }
 
-// One pair; grid = ntiles * cs CTAs in clusters of cs along x.
-template <int S>
-__global__ void __launch_bounds__(NT) plain_pair_kernel(const uint32_t* __restrict__ a, int n,
-                                                        const uint32_t* __restrict__ b, int m,
-                                                        uint32_t* __restrict__ c, ModParams mp,
-                                                        int ntiles, int cs) {
-    using C = Cfg<S>;
-    extern __shared__ uint4 smem_raw[];
-    const Smem sm = carve<S>(reinterpret_cast<uint32_t*>(smem_raw));
-    const int cluster_id = blockIdx.x / cs;
-    const int rank = blockIdx.x % cs;
-    const int tile = heavy_first(cluster_id, ntiles);
-    const int d0 = tile * C::TD;
-    const int jlo = max(0, d0 - n + 1);
-    const int jhi = min(m, d0 + C::TD);
-    const int len = max(0, jhi - jlo);
-    const int q = (((len + cs - 1) / cs) + 7) & ~7;
-    const int jb0 = min(jhi, jlo + rank * q);
-    const int jb1 = min(jhi, jb0 + q);
-
-    uint64_t acc[S];
-    tile_accumulate<S>(a, n, b, d0, jb0, jb1, mp, sm, acc);
-    cta_reduce<S>(acc, mp, sm);
-
-    const int L = n + m - 1;
-    if (cs == 1) {
-        for (int o = threadIdx.x; o < C::TD; o += NT)
-            if (d0 + o < L) c[d0 + o] = sm.red[o];
-        return;
-    }
-    cg::cluster_group cluster = cg::this_cluster();
-    cluster.sync();  // every CTA's red[] is complete and visible cluster-wide
-    const int per = C::TD / cs;
-    for (int o = rank * per + threadIdx.x; o < (rank + 1) * per; o += NT) {
-        uint64_t s = 0;
-        for (int r = 0; r < cs; ++r) s += *cluster.map_shared_rank(sm.red + o, r);
-        if (d0 + o < L) c[d0 + o] = barrett(s, mp.p, mp.mu);
-    }
-    cluster.sync();  // no CTA leaves while another still reads its shared memory
+__host__ __device__ __forceinline__ int64_t tile_jlo(int64_t n, int64_t td, int64_t t) {
+    const int64_t x = t * td - (n - 1);
+    return x > 0 ? x : 0;
 }
 
-// ---------------------------------------------------------------------------
-// Batched form: a planner kernel builds a heavy-first work list of
-// (pair, output tile) items on the device; a persistent kernel takes items
-// through one atomic counter.  Both are stream-ordered, so the pair can be
-// captured in a CUDA graph.
-// ---------------------------------------------------------------------------
-constexpr int PLAN_THREADS = 1024;
-constexpr int SORT_MAX = 16384;     // pairs sorted by cost in shared memory
+// sum_{t<T} len(t), len(t) = min(m, (t+1) td) - max(0, t td - (n-1))
+__host__ __device__ __forceinline__ int64_t cum_len(int64_t n, int64_t m, int64_t td, int64_t T) {
+    int64_t u0 = m / td;
+    if (u0 > T) u0 = T;
+    const int64_t s1 = td * (u0 * (u0 + 1) / 2) + m * (T - u0);
+    const int64_t t1 = (n - 1) / td + 1;
+    int64_t s2 = 0;
+    if (T > t1) {
+        const int64_t cnt = T - t1;
+        s2 = td * ((t1 + T - 1) * cnt / 2) - (n - 1) * cnt;
+    }
+    return s1 - s2;
+}
 
-struct BatchWs {
-    unsigned int* ctl;   // [0] next item, [1] item count
-    int* order;          // pair index of each sorted position
-    int64_t* start;      // first item of each sorted position (batch + 1 entries)
+constexpr int64_t MIN_POSITIONS = 64;  // smallest share of a CTA (positions of TD MACs each)
+
+// Scratch of one launch: 2 partial-sum slots of TD words per CTA and one
+// counter per CTA (zero between calls).
+struct SkScratch {
+    uint32_t* slots;
+    unsigned int* counters;
 };
 
-static size_t batch_ws_bytes(int64_t batch) {
-    return 256 + sizeof(int) * (size_t)((batch + 63) & ~63) + sizeof(int64_t) * (size_t)(batch + 1);
+// Partition of G positions into P ranges: the first r = G mod P ranges hold
+// q + 1 = floor(G / P) + 1 positions, the others q (q >= 1 since P <= G).
+struct Split {
+    int64_t q, r;
+    __device__ __forceinline__ int64_t start(int64_t k) const { return k * q + (k < r ? k : r); }
+    // the range holding position x
+    __device__ __forceinline__ int64_t owner(int64_t x) const {
+        const int64_t big = r * (q + 1);
+        return x < big ? x / (q + 1) : r + (x - big) / q;
+    }
+};
+
+// Persistent Stream-K kernel.  BATCH = false: one pair (a, n1, b, m1, c).
+// BATCH = true: pair i from the CSR arrays; prefix[i] = positions before pair i.
+template <int S, bool BATCH>
+__global__ void PM_BOUNDS plain_sk_kernel(
+    const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
+    const uint32_t* __restrict__ b_data, const int64_t* __restrict__ b_off,
+    uint32_t* __restrict__ c_data, const int64_t* __restrict__ c_off, int n1, int m1,
+    const int64_t* __restrict__ prefix, int batch, ModParams mp, SkScratch sk) {
+    using C = Cfg<S>;
+    extern __shared__ uint4 smem_raw[];
+    __shared__ int s_last;
+    const Smem sm = carve<S>(reinterpret_cast<uint32_t*>(smem_raw));
+    int64_t G;
+    if constexpr (BATCH) {
+        G = prefix[batch];
+    } else {
+        const int64_t nn = n1 >= m1 ? n1 : m1, mm = n1 >= m1 ? m1 : n1;
+        G = cum_len(nn, mm, C::TD, ntiles_of(nn, mm, C::TD));
+    }
+    // CTAs that would get fewer than MIN_POSITIONS positions stay idle
+    const int64_t pmax = G / MIN_POSITIONS > 1 ? G / MIN_POSITIONS : 1;
+    const int64_t P = pmax < (int64_t)gridDim.x ? pmax : (int64_t)gridDim.x;
+    const int64_t k = blockIdx.x;
+    if (k >= P) return;
+    const Split sp{G / P, G % P};
+    const int64_t x0 = sp.start(k), x1 = sp.start(k + 1);
+    int64_t x = x0;
+    // the pair holding x0 (binary search once; later segments move forward)
+    int pi = 0;
+    if constexpr (BATCH) {
+        int lo = 0, hi = batch;  // prefix[lo] <= x0 < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= x0) lo = mid; else hi = mid;
+        }
+        pi = lo;
+    }
+    int64_t t = -1;  // tile of the previous segment within pair pi (-1: search)
+    while (x < x1) {
+        int64_t pbase = 0;
+        if constexpr (BATCH) {
+            while (prefix[pi + 1] <= x) { ++pi; t = -1; }
+            pbase = prefix[pi];
+        }
+        const uint32_t *a, *b;
+        uint32_t* c;
+        int n, m;
+        if constexpr (BATCH) {
+            a = a_data + a_off[pi];
+            b = b_data + b_off[pi];
+            c = c_data + c_off[pi];
+            n = (int)(a_off[pi + 1] - a_off[pi]);
+            m = (int)(b_off[pi + 1] - b_off[pi]);
+        } else {
+            a = a_data; b = b_data; c = c_data; n = n1; m = m1;
+        }
+        if (n < m) {  // the longer operand slides through the window
+            const uint32_t* tp = a; a = b; b = tp;
+            const int tn = n; n = m; m = tn;
+        }
+        const int64_t y = x - pbase;
+        if (t >= 0) {
+            ++t;  // segments follow each other: x is the start of the next tile
+        } else {
+            int64_t tlo = 0, thi = ntiles_of(n, m, C::TD);
+            while (thi - tlo > 1) {
+                const int64_t mid = (tlo + thi) >> 1;
+                if (cum_len(n, m, C::TD, mid) <= y) tlo = mid; else thi = mid;
+            }
+            t = tlo;
+        }
+        const int64_t s_tile = pbase + cum_len(n, m, C::TD, t);
+        const int64_t e_tile = pbase + cum_len(n, m, C::TD, t + 1);
+        const int64_t seg_end = x1 < e_tile ? x1 : e_tile;
+        const int64_t jlo = tile_jlo(n, C::TD, t);
+        const int d0 = (int)(t * C::TD);
+        uint64_t acc[S];
+        tile_accumulate<S>(a, n, b, d0, (int)(jlo + (x - s_tile)), (int)(jlo + (seg_end - s_tile)),
+                           mp, sm, acc);
+        cta_reduce<S>(acc, mp, sm);
+        const int L = n + m - 1;
+        if (x == s_tile && seg_end == e_tile) {  // the whole tile is ours
+            for (int o = threadIdx.x; o < C::TD; o += NT)
+                if (d0 + o < L) c[d0 + o] = sm.red[o];
+        } else {
+            const int64_t k1 = sp.owner(s_tile), k2 = sp.owner(e_tile - 1);
+            const int64_t slot = 2 * k + (x == x0 ? 0 : 1);
+            uint32_t* mine = sk.slots + slot * C::TD;
+            for (int o = threadIdx.x; o < C::TD; o += NT) mine[o] = sm.red[o];
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned int seen = atomicAdd(&sk.counters[k1], 1u);
+                s_last = (seen == (unsigned int)(k2 - k1)) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_last) {  // every other contributor has written its slot
+                __threadfence();
+                const int64_t first_slot = 2 * k1 + (sp.start(k1) == s_tile ? 0 : 1);
+                for (int o = threadIdx.x; o < C::TD; o += NT) {
+                    uint64_t sum = __ldcg(sk.slots + first_slot * C::TD + o);
+                    for (int64_t kk = k1 + 1; kk <= k2; ++kk) sum += __ldcg(sk.slots + 2 * kk * C::TD + o);
+                    if (d0 + o < L) c[d0 + o] = barrett(sum, mp.p, mp.mu);
+                }
+                if (threadIdx.x == 0) sk.counters[k1] = 0;
+            }
+        }
+        x = seg_end;
+        if (seg_end == e_tile && e_tile == pbase + cum_len(n, m, C::TD, ntiles_of(n, m, C::TD))) t = -1;
+    }
 }
 
-static BatchWs carve_batch_ws(void* base, int64_t batch) {
-    BatchWs w;
-    w.ctl = reinterpret_cast<unsigned int*>(base);
-    w.order = reinterpret_cast<int*>(reinterpret_cast<char*>(base) + 256);
-    w.start = reinterpret_cast<int64_t*>(w.order + ((batch + 63) & ~63));
-    return w;
-}
+// ---------------------------------------------------------------------------
+// Batched form: a planner kernel validates the CSR layout and computes the
+// position prefix over pairs; the persistent kernel above does the rest.
+// Both are stream-ordered, so the pair can be captured in a CUDA graph.
+// ---------------------------------------------------------------------------
+constexpr int PLAN_THREADS = 1024;
 
 __device__ __forceinline__ bool pair_dims(int i, const int64_t* a_off, const int64_t* b_off,
                                           const int64_t* c_off, int64_t max_deg, int64_t* n,
@@ -245,69 +439,34 @@ __device__ __forceinline__ bool pair_dims(int i, const int64_t* a_off, const int
            a_off[i] >= 0 && b_off[i] >= 0 && c_off[i] >= 0;
 }
 
+__device__ __forceinline__ int64_t pair_positions(int64_t n, int64_t m, int64_t td) {
+    if (n < m) { const int64_t t = n; n = m; m = t; }
+    return cum_len(n, m, td, ntiles_of(n, m, td));
+}
+
 __global__ void __launch_bounds__(PLAN_THREADS) batch_plan_kernel(
     int batch, const int64_t* __restrict__ a_off, const int64_t* __restrict__ b_off,
-    const int64_t* __restrict__ c_off, int64_t max_deg, int td, int sort, BatchWs ws,
-    int* status) {
-    extern __shared__ unsigned long long keys[];
+    const int64_t* __restrict__ c_off, int64_t max_deg, int td, int64_t* prefix, int* status) {
     __shared__ long long s_scan[PLAN_THREADS];
     __shared__ int s_bad;
     const int tid = threadIdx.x;
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    int pow2 = 1;
-    while (pow2 < batch) pow2 <<= 1;
-    // 1. validate, and build sort keys (cost descending, then index ascending)
-    for (int i = tid; i < (sort ? pow2 : batch); i += PLAN_THREADS) {
-        if (i < batch) {
-            int64_t n, m;
-            if (!pair_dims(i, a_off, b_off, c_off, max_deg, &n, &m)) s_bad = 1;
-            if (sort) {
-                unsigned long long cost = (unsigned long long)n * (unsigned long long)m;
-                if (cost > 0xFFFFFFFFFFull) cost = 0xFFFFFFFFFFull;
-                keys[i] = ((0xFFFFFFFFFFull - cost) << 24) | (unsigned long long)i;
-            }
-        } else {
-            keys[i] = ~0ull;
-        }
-    }
-    __syncthreads();
-    if (s_bad) {
-        if (tid == 0) {
-            atomicCAS(status, 0, (int)PM_ERR_INVALID_ARG);
-            ws.ctl[0] = 0;
-            ws.ctl[1] = 0;
-        }
-        return;
-    }
-    // 2. bitonic sort of the keys (ascending = heaviest first)
-    if (sort) {
-        for (int k = 2; k <= pow2; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int i = tid; i < pow2; i += PLAN_THREADS) {
-                    const int ixj = i ^ j;
-                    if (ixj > i) {
-                        const unsigned long long x = keys[i], y = keys[ixj];
-                        const bool up = (i & k) == 0;
-                        if ((x > y) == up) { keys[i] = y; keys[ixj] = x; }
-                    }
-                }
-                __syncthreads();
-            }
-        }
-    }
-    // 3. exclusive scan of tile counts in sorted order (blocked: each thread a run)
     const int per = (batch + PLAN_THREADS - 1) / PLAN_THREADS;
     const int lo = min(batch, tid * per), hi = min(batch, lo + per);
     long long run = 0;
-    for (int k = lo; k < hi; ++k) {
-        const int i = sort ? (int)(keys[k] & 0xFFFFFF) : k;
+    for (int i = lo; i < hi; ++i) {
         int64_t n, m;
-        pair_dims(i, a_off, b_off, c_off, max_deg, &n, &m);
-        run += (n + m - 1 + td - 1) / td;
+        if (!pair_dims(i, a_off, b_off, c_off, max_deg, &n, &m)) { s_bad = 1; continue; }
+        run += pair_positions(n, m, td);
     }
     s_scan[tid] = run;
     __syncthreads();
+    if (s_bad) {  // nothing is computed: G = 0
+        for (int i = tid; i <= batch; i += PLAN_THREADS) prefix[i] = 0;
+        if (tid == 0) atomicCAS(status, 0, (int)PM_ERR_INVALID_ARG);
+        return;
+    }
     for (int off = 1; off < PLAN_THREADS; off <<= 1) {
         const long long v = tid >= off ? s_scan[tid - off] : 0;
         __syncthreads();
@@ -315,114 +474,84 @@ __global__ void __launch_bounds__(PLAN_THREADS) batch_plan_kernel(
         __syncthreads();
     }
     long long pos = s_scan[tid] - run;
-    for (int k = lo; k < hi; ++k) {
-        const int i = sort ? (int)(keys[k] & 0xFFFFFF) : k;
+    for (int i = lo; i < hi; ++i) {
         int64_t n, m;
         pair_dims(i, a_off, b_off, c_off, max_deg, &n, &m);
-        ws.order[k] = i;
-        ws.start[k] = pos;
-        pos += (n + m - 1 + td - 1) / td;
+        prefix[i] = pos;
+        pos += pair_positions(n, m, td);
     }
-    if (tid == PLAN_THREADS - 1) {
-        ws.start[batch] = s_scan[PLAN_THREADS - 1];
-        ws.ctl[0] = 0;
-        const long long total = s_scan[PLAN_THREADS - 1];
-        ws.ctl[1] = total > 0x7FFFFFFF ? 0u : (unsigned int)total;
-        if (total > 0x7FFFFFFF) atomicCAS(status, 0, (int)PM_ERR_RANGE);
-    }
-}
-
-template <int S>
-__global__ void __launch_bounds__(NT) plain_batched_kernel(
-    int batch, const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
-    const uint32_t* __restrict__ b_data, const int64_t* __restrict__ b_off,
-    uint32_t* __restrict__ c_data, const int64_t* __restrict__ c_off, ModParams mp, BatchWs ws) {
-    using C = Cfg<S>;
-    extern __shared__ uint4 smem_raw[];
-    const Smem sm = carve<S>(reinterpret_cast<uint32_t*>(smem_raw));
-    __shared__ int s_item;
-    const unsigned int total = *(volatile unsigned int*)&ws.ctl[1];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(&ws.ctl[0], 1u);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if ((unsigned int)item >= total) break;
-        // sorted position k: the last k with start[k] <= item
-        int lo = 0, hi = batch;  // start[lo] <= item < start[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (ws.start[mid] <= item) lo = mid; else hi = mid;
-        }
-        const int pair = ws.order[lo];
-        const int tile = (int)(item - ws.start[lo]);
-        int n = (int)(a_off[pair + 1] - a_off[pair]);
-        int m = (int)(b_off[pair + 1] - b_off[pair]);
-        const uint32_t* a = a_data + a_off[pair];
-        const uint32_t* b = b_data + b_off[pair];
-        if (n < m) {  // the longer operand slides through the window
-            const uint32_t* t = a; a = b; b = t;
-            const int tn = n; n = m; m = tn;
-        }
-        const int d0 = tile * C::TD;
-        const int jlo = max(0, d0 - n + 1);
-        const int jhi = min(m, d0 + C::TD);
-        uint64_t acc[S];
-        tile_accumulate<S>(a, n, b, d0, jlo, jhi, mp, sm, acc);
-        cta_reduce<S>(acc, mp, sm);
-        const int L = n + m - 1;
-        uint32_t* c = c_data + c_off[pair];
-        for (int o = threadIdx.x; o < C::TD; o += NT)
-            if (d0 + o < L) c[d0 + o] = sm.red[o];
-    }
+    if (tid == PLAN_THREADS - 1) prefix[batch] = s_scan[PLAN_THREADS - 1];
 }
 
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
+
+// Raises the kernel's dynamic shared-memory limit and caches its occupancy,
+// once per device (cache[dev] = blocks per SM, 0 = not yet set up).
+template <typename K>
+static cudaError_t kernel_setup(K kern, size_t smem, int dev, int* cache, int* occ,
+                                int threads = NT) {
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) {
+        *occ = cache[dev];
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int o = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, threads, smem);
+    if (e != cudaSuccess) return e;
+    o = std::max(o, 1);
+    if (dev >= 0 && dev < 64) cache[dev] = o;
+    *occ = o;
+    return cudaSuccess;
+}
+
+// Scratch layout: COUNTER_MAX counters (zeroed when the buffer is allocated and
+// returned to zero by every call), then 2 P slots of TD words.
+constexpr int64_t COUNTER_MAX = 4096;
+constexpr size_t COUNTER_BYTES = COUNTER_MAX * sizeof(unsigned int);
+
+static size_t sk_bytes(int64_t P, int td) {
+    return COUNTER_BYTES + (size_t)(2 * P * td) * sizeof(uint32_t);
+}
+
+static SkScratch sk_carve(void* base) {
+    SkScratch s;
+    s.counters = reinterpret_cast<unsigned int*>(base);
+    s.slots = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(base) + COUNTER_BYTES);
+    return s;
+}
+
 template <int S>
 static pm_status launch_pair_s(const uint32_t* a, int n, const uint32_t* b, int m, uint32_t* c,
-                               uint32_t p, cudaStream_t st, const DeviceWorkspace* ws) {
+                               uint32_t p, cudaStream_t st, DeviceWorkspace* ws) {
     using C = Cfg<S>;
-    auto kern = plain_pair_kernel<S>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)C::SMEM);
+    auto kern = plain_sk_kernel<S, false>;
+    static int occ_cache[64] = {};
+    int occ = 0;
+    cudaError_t e = kernel_setup(kern, C::SMEM, ws->device, occ_cache, &occ);
     if (e != cudaSuccess) return cuda_fail(e);
-    int occ = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, C::SMEM);
-    if (e != cudaSuccess) return cuda_fail(e);
-    occ = std::max(occ, 1);
-    const int L = n + m - 1;
-    const int ntiles = (L + C::TD - 1) / C::TD;
-    const int want = 2 * ws->num_sms * occ;
-    int cs = 1;
-    while (cs < 8 && ntiles * cs < want && (std::min(n, m) / (cs * 2)) >= 256) cs *= 2;
+    const int64_t nn = std::max(n, m), mm = std::min(n, m);
+    const int64_t G = cum_len(nn, mm, C::TD, ntiles_of(nn, mm, C::TD));
+    const int64_t P = std::min<int64_t>(std::min<int64_t>((int64_t)ws->num_sms * occ, COUNTER_MAX),
+                                        std::max<int64_t>(1, G / MIN_POSITIONS));
+    StreamScratch* sc = nullptr;
+    pm_status rc = stream_scratch(ws, st, &sc);
+    if (rc != PM_OK) return rc;
+    rc = ensure_scratch(&sc->sk, &sc->sk_bytes, sk_bytes(P, C::TD), st, /*zero=*/true);
+    if (rc != PM_OK) return rc;
     const ModParams mp = host_mod_params(p, C::KB);
-
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3((unsigned)(ntiles * cs));
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = C::SMEM;
-    cfg.stream = st;
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, kern, a, n, b, m, c, mp, ntiles, cs);
+    kern<<<(unsigned)P, NT, C::SMEM, st>>>(a, nullptr, b, nullptr, c, nullptr, n, m, nullptr, 0, mp,
+                                           sk_carve(sc->sk));
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     count_launches(1);
     return PM_OK;
 }
 
 pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c,
-                       uint32_t p, int s, cudaStream_t st, const DeviceWorkspace* ws) {
-    if (n < m) {  // the longer operand slides through the window
-        std::swap(a, b);
-        std::swap(n, m);
-    }
+                       uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws) {
     const int ni = (int)n, mi = (int)m;
     switch (s) {
         case 1: return launch_pair_s<1>(a, ni, b, mi, c, p, st, ws);
@@ -442,35 +571,27 @@ static pm_status launch_batched_s(int64_t batch, const uint32_t* a_data, const i
                                   const int64_t* c_off, uint32_t p, int64_t max_deg,
                                   cudaStream_t st, DeviceWorkspace* ws) {
     using C = Cfg<S>;
-    pm_status rc = ensure_buffer(&ws->batch_ws, &ws->batch_ws_bytes, batch_ws_bytes(batch), st);
-    if (rc != PM_OK) return rc;
-    const BatchWs bw = carve_batch_ws(ws->batch_ws, batch);
-    const int sort = batch <= SORT_MAX ? 1 : 0;
-    size_t plan_smem = 0;
-    if (sort) {
-        size_t pow2 = 1;
-        while ((int64_t)pow2 < batch) pow2 <<= 1;
-        plan_smem = pow2 * sizeof(unsigned long long);
-    }
-    cudaError_t e = cudaFuncSetAttribute(batch_plan_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max<size_t>(plan_smem, 1));
+    auto kern = plain_sk_kernel<S, true>;
+    static int occ_cache[64] = {};
+    int occ = 0;
+    cudaError_t e = kernel_setup(kern, C::SMEM, ws->device, occ_cache, &occ);
     if (e != cudaSuccess) return cuda_fail(e);
-    batch_plan_kernel<<<1, PLAN_THREADS, plan_smem, st>>>((int)batch, a_off, b_off, c_off,
-                                                          max_deg, C::TD, sort, bw, ws->status);
+    const int64_t P = std::min<int64_t>((int64_t)ws->num_sms * occ, COUNTER_MAX);
+    StreamScratch* sc = nullptr;
+    pm_status rc = stream_scratch(ws, st, &sc);
+    if (rc != PM_OK) return rc;
+    rc = ensure_scratch(&sc->sk, &sc->sk_bytes, sk_bytes(P, C::TD), st, /*zero=*/true);
+    if (rc != PM_OK) return rc;
+    rc = ensure_scratch(&sc->plan, &sc->plan_bytes, sizeof(int64_t) * (size_t)(batch + 1), st, false);
+    if (rc != PM_OK) return rc;
+    int64_t* prefix = reinterpret_cast<int64_t*>(sc->plan);
+    batch_plan_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg, C::TD,
+                                                  prefix, ws->status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
-
-    auto kern = plain_batched_kernel<S>;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
-    if (e != cudaSuccess) return cuda_fail(e);
-    int occ = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, C::SMEM);
-    if (e != cudaSuccess) return cuda_fail(e);
-    occ = std::max(occ, 1);
     const ModParams mp = host_mod_params(p, C::KB);
-    kern<<<ws->num_sms * occ, NT, C::SMEM, st>>>((int)batch, a_data, a_off, b_data, b_off, c_data,
-                                                 c_off, mp, bw);
+    kern<<<(unsigned)P, NT, C::SMEM, st>>>(a_data, a_off, b_data, b_off, c_data, c_off, 0, 0, prefix,
+                                           (int)batch, mp, sk_carve(sc->sk));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     count_launches(2);
