@@ -371,7 +371,9 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
     b = torch.from_numpy(b_np).to(dev)
     c = torch.empty(2 * N_SINGLE - 1, dtype=torch.uint32, device=dev)
     ell = 256
-    U = 256.0 * SM_MAX_MHZ * 1e6 * SMS / (pk["hbm_gbs"] * 1e9)  # word move / local op (see DESIGN)
+    # U: time to move one 4-byte word per SM (HBM share) over the time of one
+    # local multiply-add, both per SM: (ops/clk/SM * 4 B * clk * SMs) / (HBM bytes/s)
+    U = 4.0 * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6 * SMS / (pk["hbm_gbs"] * 1e9)
     unit_s = ell / (IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6)         # one local op of a whole block
     sweep = []
     for s in pm.S_CANDIDATES:

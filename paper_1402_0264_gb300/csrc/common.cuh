@@ -108,6 +108,7 @@ pm_status stream_scratch(DeviceWorkspace* ws, cudaStream_t st, StreamScratch** o
 pm_status ensure_scratch(void** buf, size_t* have, size_t bytes, cudaStream_t st, bool zero);
 
 pm_status cuda_fail(cudaError_t e);
+void release_ntt_tables();
 void count_launches(uint64_t k);
 bool is_capturing(void* stream);
 

@@ -1,9 +1,414 @@
-// Number-theoretic-transform path (filled in below).
+// Number-theoretic-transform form of the product (large degrees).
+//
+// c = a*b mod p as the inverse transform of the pointwise product of the
+// length-N transforms of a and b (N = 2^k >= n+m-1, N | p-1), scaled by N^-1.
+// The paper has no transform path; the result is the same exact residues as
+// the long multiplication of Section 5.
+//
+// Layout of a length-N transform, N = N1 * N2 with N2 = 4096 when N > 4096
+// (four-step decomposition; n = n1 N2 + n2, k = k1 + N1 k2):
+//   X[k1 + N1 k2] = sum_n2 w_N2^(n2 k2) w_N^(n2 k1) sum_n1 x[n1 N2 + n2] w_N1^(n1 k1)
+// 1. column pass: for each column n2 a length-N1 transform over n1, times
+//    w_N^(n2 k1); a and b in one launch, written to two scratch arrays;
+// 2. row pass (fused): per row, the length-N2 transforms of both arrays, the
+//    pointwise product, the inverse length-N2 transform and w_N^(-n2 k1);
+// 3. inverse column pass: per column the inverse length-N1 transform, the
+//    scale N^-1, and the store of the n+m-1 output words.
+// Every pass reads and writes each word once (3 HBM round trips in all).
+// Inside a pass the transforms run in shared memory: forward transforms are
+// decimation in frequency (natural order in, digit-reversed out), inverse
+// ones decimation in time (digit-reversed in, natural out), with radix-4
+// butterflies and one radix-2 stage when log2 of the length is odd, so no
+// reordering pass is needed.  N <= 4096 runs in one CTA per product.
+//
+// Arithmetic: values stay in [0, p), p < 2^30.  Multiplication by a table
+// constant w uses Shoup's precomputed quotient wq = floor(w 2^32 / p)
+// (V. Shoup, NTL; also D. Harvey, "Faster arithmetic for number-theoretic
+// transforms", J. Symb. Comp. 2014): q = hi32(x wq), r = x w - q p in [0, 2p).
+// The pointwise product uses Montgomery reduction (P. Montgomery,
+// "Modular multiplication without trial division", Math. Comp. 1985) with
+// R = 2^32; the extra factor 2^-32 is folded into the final scale
+// N^-1 2^32 mod p.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "common.cuh"
 
 namespace pm {
-pm_status launch_ntt(const uint32_t*, int64_t, const uint32_t*, int64_t, uint32_t*, uint32_t,
-                     uint32_t, cudaStream_t, DeviceWorkspace*) {
-    return PM_ERR_UNSUPPORTED;
+
+constexpr int NTT_N2_LOG = 12;               // row length of the four-step layout
+constexpr int NTT_N2 = 1 << NTT_N2_LOG;
+constexpr int NTT_MAX_LOG = 24;              // N1 <= 4096 keeps a column block in shared memory
+constexpr int COLS = 8;                      // columns per CTA in the column passes
+constexpr int NTT_THREADS = 512;
+
+struct NttMod {
+    uint32_t p;
+    uint32_t pinv_neg;  // -p^-1 mod 2^32
+};
+
+__device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint32_t add_p(uint32_t x, uint32_t y, uint32_t p) {
+    const uint32_t s = x + y;
+    return umin32(s, s - p);
 }
+__device__ __forceinline__ uint32_t sub_p(uint32_t x, uint32_t y, uint32_t p) {
+    const uint32_t d = x - y + p;
+    return umin32(d, d - p);
+}
+__device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint2 w, uint32_t p) {
+    const uint32_t q = __umulhi(x, w.y);
+    const uint32_t r = x * w.x - q * p;
+    return umin32(r, r - p);
+}
+__device__ __forceinline__ uint32_t mul_mont(uint32_t x, uint32_t y, const NttMod& m) {
+    const uint64_t t = (uint64_t)x * y;
+    const uint32_t q = (uint32_t)t * m.pinv_neg;
+    const uint32_t u = (uint32_t)((t + (uint64_t)q * m.p) >> 32);
+    return umin32(u, u - m.p);
+}
+
+// Frequency index k of output position `pos` of a forward transform of
+// length 2^logm (stage radices 2 (odd logm only) then 4, 4, ...).
+__host__ __device__ __forceinline__ int freq_of_pos(int pos, int logm) {
+    int k = 0, mult = 1, lg = logm, rem = pos;
+    if (lg & 1) {
+        --lg;
+        k += (rem >> lg) * mult;
+        rem &= (1 << lg) - 1;
+        mult <<= 1;
+    }
+    while (lg > 0) {
+        lg -= 2;
+        k += (rem >> lg) * mult;
+        rem &= (1 << lg) - 1;
+        mult <<= 2;
+    }
+    return k;
+}
+
+// In-place transforms of `cnt` arrays (base + t*stride, length 2^logm) in
+// shared memory by the whole CTA.  tw[e] = w_M^e (forward) or w_M^-e
+// (inverse) for e in [0, M), with its Shoup quotient.
+template <bool FWD>
+__device__ void smem_ntt(uint32_t* base, int stride, int cnt, int logm, const uint2* __restrict__ tw,
+                         uint32_t p) {
+    const int M = 1 << logm;
+    const uint2 w4 = __ldg(tw + (M >> 2));  // primitive 4th root (or its inverse)
+    const int quarter = M >> 2;
+    const int nbf4 = cnt * quarter;
+    if (FWD && (logm & 1)) {  // radix-2 stage, span M/2
+        const int h = M >> 1;
+        for (int idx = threadIdx.x; idx < cnt * h; idx += blockDim.x) {
+            const int t = idx >> (logm - 1), j = idx & (h - 1);
+            uint32_t* x = base + t * stride;
+            const uint32_t u = x[j], v = x[j + h];
+            x[j] = add_p(u, v, p);
+            x[j + h] = mul_shoup(sub_p(u, v, p), __ldg(tw + j), p);
+        }
+        __syncthreads();
+    }
+    const int smax = (logm & 1) ? (M >> 3) : (M >> 2);
+    for (int it = 0, s = FWD ? smax : 1; FWD ? s >= 1 : s <= smax; ++it, s = FWD ? (s >> 2) : (s << 2)) {
+        const int lgs = FWD ? (logm & 1 ? logm - 3 : logm - 2) - 2 * it : 2 * it;  // log2 s
+        const int lgstep = logm - 2 - lgs;  // twiddle exponent step M/(4s)
+        for (int idx = threadIdx.x; idx < nbf4; idx += blockDim.x) {
+            const int t = idx >> (logm - 2), b = idx & (quarter - 1);
+            const int blk = b >> lgs, j = b & (s - 1);
+            uint32_t* x = base + t * stride + (blk << (lgs + 2)) + j;
+            const int e = j << lgstep;
+            uint32_t x0 = x[0], x1 = x[s], x2 = x[2 * s], x3 = x[3 * s];
+            if (!FWD) {  // decimation in time: twiddle the inputs
+                x1 = mul_shoup(x1, __ldg(tw + e), p);
+                x2 = mul_shoup(x2, __ldg(tw + 2 * e), p);
+                x3 = mul_shoup(x3, __ldg(tw + 3 * e), p);
+            }
+            const uint32_t t0 = add_p(x0, x2, p), t1 = sub_p(x0, x2, p);
+            const uint32_t t2 = add_p(x1, x3, p), t3 = mul_shoup(sub_p(x1, x3, p), w4, p);
+            uint32_t z0 = add_p(t0, t2, p), z2 = sub_p(t0, t2, p);
+            uint32_t z1 = add_p(t1, t3, p), z3 = sub_p(t1, t3, p);
+            if (FWD) {  // decimation in frequency: twiddle the outputs
+                z1 = mul_shoup(z1, __ldg(tw + e), p);
+                z2 = mul_shoup(z2, __ldg(tw + 2 * e), p);
+                z3 = mul_shoup(z3, __ldg(tw + 3 * e), p);
+            }
+            x[0] = z0; x[s] = z1; x[2 * s] = z2; x[3 * s] = z3;
+        }
+        __syncthreads();
+    }
+    if (!FWD && (logm & 1)) {  // radix-2 stage, span M/2
+        const int h = M >> 1;
+        for (int idx = threadIdx.x; idx < cnt * h; idx += blockDim.x) {
+            const int t = idx >> (logm - 1), j = idx & (h - 1);
+            uint32_t* x = base + t * stride;
+            const uint32_t u = x[j], v = mul_shoup(x[j + h], __ldg(tw + j), p);
+            x[j] = add_p(u, v, p);
+            x[j + h] = sub_p(u, v, p);
+        }
+        __syncthreads();
+    }
+}
+
+// Device tables of one (p, g, log N), each entry (w, floor(w 2^32 / p)).
+struct NttTables {
+    const uint2 *lo, *ilo;    // w_N^e, w_N^-e, e < 4096
+    const uint2 *row, *irow;  // w_N2^e, w_N2^-e, e < 4096 (N > 4096)
+    const uint2 *hi, *ihi;    // w_N^(4096 f), w_N^(-4096 f), f < N1 (= w_N1^f)
+    uint2 scale;              // N^-1 2^32 mod p
+    uint32_t w4_unused;
+};
+
+// x * w_N^e (or w_N^-e) with e < N: w_N^e = lo[e mod 4096] * hi[e / 4096].
+__device__ __forceinline__ uint32_t mul_root(uint32_t x, uint32_t e, const uint2* lo, const uint2* hi,
+                                             uint32_t p) {
+    return mul_shoup(mul_shoup(x, __ldg(lo + (e & (NTT_N2 - 1))), p), __ldg(hi + (e >> NTT_N2_LOG)), p);
+}
+
+// ---- N <= 4096: one CTA per product ----
+__global__ void __launch_bounds__(NTT_THREADS) ntt_small_kernel(
+    const uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ b, int m,
+    uint32_t* __restrict__ c, int logn, NttTables tb, NttMod md) {
+    extern __shared__ uint32_t sh[];
+    const int N = 1 << logn, L = n + m - 1;
+    uint32_t* sa = sh;
+    uint32_t* sb = sh + N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        sa[i] = i < n ? a[i] : 0u;
+        sb[i] = i < m ? b[i] : 0u;
+    }
+    __syncthreads();
+    smem_ntt<true>(sh, N, 2, logn, tb.lo, md.p);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sa[i] = mul_mont(sa[i], sb[i], md);
+    __syncthreads();
+    smem_ntt<false>(sa, N, 1, logn, tb.ilo, md.p);
+    for (int i = threadIdx.x; i < L; i += blockDim.x) c[i] = mul_shoup(sa[i], tb.scale, md.p);
+}
+
+// ---- four-step pass 1: forward column transforms of a (y = 0) and b (y = 1) ----
+__global__ void __launch_bounds__(NTT_THREADS) ntt_col_fwd_kernel(
+    const uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ b, int m,
+    uint32_t* __restrict__ ta, uint32_t* __restrict__ tb_out, int logn1, NttTables tb, NttMod md) {
+    extern __shared__ uint32_t sh[];
+    const int N1 = 1 << logn1, stride = N1 + 1;
+    const uint32_t* x = blockIdx.y == 0 ? a : b;
+    const int len = blockIdx.y == 0 ? n : m;
+    uint32_t* out = blockIdx.y == 0 ? ta : tb_out;
+    const int c0 = blockIdx.x * COLS;
+    for (int idx = threadIdx.x; idx < COLS * N1; idx += blockDim.x) {
+        const int j = idx & (COLS - 1), n1 = idx / COLS;
+        const int g = n1 * NTT_N2 + c0 + j;
+        sh[j * stride + n1] = g < len ? __ldg(x + g) : 0u;
+    }
+    __syncthreads();
+    smem_ntt<true>(sh, stride, COLS, logn1, tb.hi, md.p);
+    for (int idx = threadIdx.x; idx < COLS * N1; idx += blockDim.x) {
+        const int j = idx & (COLS - 1), pos = idx / COLS;
+        const uint32_t k1 = (uint32_t)freq_of_pos(pos, logn1);
+        const uint32_t e = (uint32_t)(((uint64_t)(c0 + j) * k1) & ((((uint64_t)N1) << NTT_N2_LOG) - 1));
+        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root(sh[j * stride + pos], e, tb.lo, tb.hi, md.p);
+    }
+}
+
+// ---- four-step pass 2: per row, forward row transforms, product, inverse ----
+__global__ void __launch_bounds__(NTT_THREADS) ntt_row_kernel(uint32_t* __restrict__ ta,
+                                                              const uint32_t* __restrict__ tbuf,
+                                                              int logn1, NttTables tb, NttMod md) {
+    __shared__ uint32_t sh[2 * NTT_N2];
+    const size_t r0 = (size_t)blockIdx.x * NTT_N2;
+    for (int i = threadIdx.x; i < NTT_N2; i += blockDim.x) {
+        sh[i] = ta[r0 + i];
+        sh[NTT_N2 + i] = tbuf[r0 + i];
+    }
+    __syncthreads();
+    smem_ntt<true>(sh, NTT_N2, 2, NTT_N2_LOG, tb.row, md.p);
+    for (int i = threadIdx.x; i < NTT_N2; i += blockDim.x) sh[i] = mul_mont(sh[i], sh[NTT_N2 + i], md);
+    __syncthreads();
+    smem_ntt<false>(sh, NTT_N2, 1, NTT_N2_LOG, tb.irow, md.p);
+    const uint32_t k1 = (uint32_t)freq_of_pos(blockIdx.x, logn1);
+    const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
+    for (int i = threadIdx.x; i < NTT_N2; i += blockDim.x) {
+        const uint32_t e = (uint32_t)(((uint64_t)i * k1) & nmask);
+        ta[r0 + i] = mul_root(sh[i], e, tb.ilo, tb.ihi, md.p);
+    }
+}
+
+// ---- four-step pass 3: inverse column transforms, scale, store ----
+__global__ void __launch_bounds__(NTT_THREADS) ntt_col_inv_kernel(const uint32_t* __restrict__ ta,
+                                                                  uint32_t* __restrict__ c, int L,
+                                                                  int logn1, NttTables tb, NttMod md) {
+    extern __shared__ uint32_t sh[];
+    const int N1 = 1 << logn1, stride = N1 + 1;
+    const int c0 = blockIdx.x * COLS;
+    for (int idx = threadIdx.x; idx < COLS * N1; idx += blockDim.x) {
+        const int j = idx & (COLS - 1), pos = idx / COLS;
+        sh[j * stride + pos] = ta[(size_t)pos * NTT_N2 + c0 + j];
+    }
+    __syncthreads();
+    smem_ntt<false>(sh, stride, COLS, logn1, tb.ihi, md.p);
+    for (int idx = threadIdx.x; idx < COLS * N1; idx += blockDim.x) {
+        const int j = idx & (COLS - 1), n1 = idx / COLS;
+        const int64_t g = (int64_t)n1 * NTT_N2 + c0 + j;
+        if (g < L) c[g] = mul_shoup(sh[j * stride + n1], tb.scale, md.p);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+static uint32_t powmod_h(uint64_t b, uint64_t e, uint32_t p) {
+    uint64_t r = 1 % p;
+    b %= p;
+    while (e) {
+        if (e & 1) r = r * b % p;
+        b = b * b % p;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+
+static uint2 shoup_pair(uint32_t w, uint32_t p) {
+    return make_uint2(w, (uint32_t)((((uint64_t)w) << 32) / p));
+}
+
+struct TableSet {
+    uint2* dev = nullptr;
+    NttTables t{};
+};
+
+static std::mutex g_tab_mutex;
+static std::map<std::tuple<int, uint32_t, uint32_t, int>, TableSet> g_tables;
+
+// Builds (once) the twiddle tables of (device, p, g, logn) with a synchronous copy.
+static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStream_t st, NttTables* out) {
+    std::lock_guard<std::mutex> lock(g_tab_mutex);
+    auto key = std::make_tuple(dev, p, g, logn);
+    auto it = g_tables.find(key);
+    if (it != g_tables.end()) {
+        *out = it->second.t;
+        return PM_OK;
+    }
+    if (is_capturing(st)) return PM_ERR_UNSUPPORTED;
+    const uint64_t N = 1ull << logn;
+    const uint32_t w = powmod_h(g, (uint64_t)(p - 1) / N, p);
+    if (N >= 2 && powmod_h(w, N / 2, p) != p - 1) return PM_ERR_UNSUPPORTED;  // not of order N
+    const uint32_t wi = powmod_h(w, p - 2, p);
+    const int n1 = logn > NTT_N2_LOG ? (int)(N >> NTT_N2_LOG) : 1;
+    const size_t words = 4 * NTT_N2 + 2 * (size_t)n1;
+    std::vector<uint2> h(words);
+    uint2* lo = h.data();
+    uint2* ilo = lo + NTT_N2;
+    uint2* row = ilo + NTT_N2;
+    uint2* irow = row + NTT_N2;
+    uint2* hi = irow + NTT_N2;
+    uint2* ihi = hi + n1;
+    for (int e = 0; e < NTT_N2; ++e) {
+        lo[e] = shoup_pair(powmod_h(w, (uint64_t)e % N, p), p);
+        ilo[e] = shoup_pair(powmod_h(wi, (uint64_t)e % N, p), p);
+        row[e] = shoup_pair(powmod_h(w, ((uint64_t)n1 * e) % N, p), p);
+        irow[e] = shoup_pair(powmod_h(wi, ((uint64_t)n1 * e) % N, p), p);
+    }
+    for (int f = 0; f < n1; ++f) {
+        hi[f] = shoup_pair(powmod_h(w, ((uint64_t)NTT_N2 * f) % N, p), p);
+        ihi[f] = shoup_pair(powmod_h(wi, ((uint64_t)NTT_N2 * f) % N, p), p);
+    }
+    TableSet ts;
+    if (cudaMalloc((void**)&ts.dev, words * sizeof(uint2)) != cudaSuccess) {
+        cudaGetLastError();
+        return PM_ERR_NOMEM;
+    }
+    cudaError_t e = cudaMemcpy(ts.dev, h.data(), words * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(ts.dev);
+        return cuda_fail(e);
+    }
+    ts.t.lo = ts.dev;
+    ts.t.ilo = ts.dev + NTT_N2;
+    ts.t.row = ts.dev + 2 * NTT_N2;
+    ts.t.irow = ts.dev + 3 * NTT_N2;
+    ts.t.hi = ts.dev + 4 * NTT_N2;
+    ts.t.ihi = ts.t.hi + n1;
+    // N^-1 * 2^32 mod p cancels the Montgomery factor of the pointwise product
+    const uint32_t ninv = powmod_h(N % p, p - 2, p);
+    const uint32_t r32 = (uint32_t)((1ull << 32) % p);
+    ts.t.scale = shoup_pair((uint32_t)((uint64_t)ninv * r32 % p), p);
+    g_tables[key] = ts;
+    *out = ts.t;
+    return PM_OK;
+}
+
+void release_ntt_tables() {
+    std::lock_guard<std::mutex> lock(g_tab_mutex);
+    for (auto& kv : g_tables) cudaFree(kv.second.dev);
+    g_tables.clear();
+}
+
+pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c,
+                     uint32_t p, uint32_t g, cudaStream_t st, DeviceWorkspace* ws) {
+    if (g == 0) {
+        if (p != 469762049u) return PM_ERR_UNSUPPORTED;  // generator known for 7*2^26+1 only
+        g = 3;
+    }
+    if (g >= p) return PM_ERR_INVALID_ARG;
+    const int64_t L = n + m - 1;
+    int logn = 0;
+    while ((1ll << logn) < L) ++logn;
+    if (logn > NTT_MAX_LOG) return PM_ERR_RANGE;
+    if (logn < 2) logn = 2;
+    if ((uint64_t)(p - 1) % (1ull << logn) != 0) return PM_ERR_UNSUPPORTED;
+    NttTables tb;
+    pm_status rc = get_tables(ws->device, p, g, logn, st, &tb);
+    if (rc != PM_OK) return rc;
+    NttMod md;
+    md.p = p;
+    uint32_t inv = 1;  // p^-1 mod 2^32 by Newton iteration (p odd)
+    for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
+    md.pinv_neg = 0u - inv;
+    cudaError_t e;
+    if (logn <= NTT_N2_LOG) {
+        const size_t smem = 2 * sizeof(uint32_t) * ((size_t)1 << logn);
+        static int done[64] = {};
+        if (!done[ws->device]) {
+            e = cudaFuncSetAttribute(ntt_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(2 * sizeof(uint32_t) * NTT_N2));
+            if (e != cudaSuccess) return cuda_fail(e);
+            done[ws->device] = 1;
+        }
+        ntt_small_kernel<<<1, NTT_THREADS, smem, st>>>(a, (int)n, b, (int)m, c, logn, tb, md);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+        count_launches(1);
+        return PM_OK;
+    }
+    const int logn1 = logn - NTT_N2_LOG;
+    const size_t N = (size_t)1 << logn;
+    StreamScratch* sc = nullptr;
+    rc = stream_scratch(ws, st, &sc);
+    if (rc != PM_OK) return rc;
+    rc = ensure_scratch(&sc->ntt, &sc->ntt_bytes, 2 * N * sizeof(uint32_t), st, false);
+    if (rc != PM_OK) return rc;
+    uint32_t* ta = reinterpret_cast<uint32_t*>(sc->ntt);
+    uint32_t* tbuf = ta + N;
+    const size_t col_smem = sizeof(uint32_t) * (size_t)COLS * (((size_t)1 << logn1) + 1);
+    static int col_done[64] = {};
+    if (!col_done[ws->device]) {
+        const int mx = (int)(sizeof(uint32_t) * COLS * ((1 << (NTT_MAX_LOG - NTT_N2_LOG)) + 1));
+        e = cudaFuncSetAttribute(ntt_col_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaFuncSetAttribute(ntt_col_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        if (e != cudaSuccess) return cuda_fail(e);
+        col_done[ws->device] = 1;
+    }
+    ntt_col_fwd_kernel<<<dim3(NTT_N2 / COLS, 2), NTT_THREADS, col_smem, st>>>(a, (int)n, b, (int)m, ta,
+                                                                            tbuf, logn1, tb, md);
+    ntt_row_kernel<<<1u << logn1, NTT_THREADS, 0, st>>>(ta, tbuf, logn1, tb, md);
+    ntt_col_inv_kernel<<<NTT_N2 / COLS, NTT_THREADS, col_smem, st>>>(ta, c, (int)L, logn1, tb, md);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(3);
+    return PM_OK;
+}
+
 }  // namespace pm
