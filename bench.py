@@ -430,6 +430,37 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
                              "macs": macs, "ms_graph": ms_g, "ms_direct": best[1],
                              "macs_per_s": macs / (ms_g * 1e-3), "products_per_s": 4096 / (ms_g * 1e-3),
                              "alu_frac": macs / (ms_g * 1e-3) / alu_peak_macs()}
+
+    # --- transform path: one pair of degree 2^22 - 1, and the plain/transform crossover ---
+    an, bn = inputs.workload_ntt()
+    dan, dbn = torch.from_numpy(an).to(dev), torch.from_numpy(bn).to(dev)
+    cn = torch.empty(2 * len(an) - 1, dtype=torch.uint32, device=dev)
+    pm.ntt(dan, dbn, out=cn)
+    ms_n = median_ms(lambda: pm.ntt(dan, dbn, out=cn), 20, flush, stream)
+    assert np.array_equal(cn.cpu().numpy().view(np.uint32), oracle.ntt_polymul(an, bn, P))
+    nn = len(an)
+    algo_bytes = 4 * (2 * nn + 2 * nn - 1)  # read a and b, write c
+    rows["ntt"] = {"workload": "one pair of degree 2^22-1 (transform length 2^23)", "ms": ms_n,
+                   "schoolbook_equiv_macs_per_s": nn * nn / (ms_n * 1e-3),
+                   "products_per_s": 1.0 / (ms_n * 1e-3),
+                   "algorithmic_bytes": algo_bytes,
+                   "algorithmic_gbs": algo_bytes / (ms_n * 1e-3) / 1e9,
+                   "hbm_frac_algorithmic": algo_bytes / (ms_n * 1e-3) / 1e9 / pk["hbm_gbs"]}
+    sweep = []
+    for logn in range(10, 23):
+        n_ = 1 << logn
+        a_, b_ = inputs.workload_ntt(deg=n_ - 1, seed=inputs.SEED_BASE + 40 + logn)
+        da_, db_ = torch.from_numpy(a_).to(dev), torch.from_numpy(b_).to(dev)
+        c_ = torch.empty(2 * n_ - 1, dtype=torch.uint32, device=dev)
+        pm.ntt(da_, db_, out=c_)
+        t_ntt = median_ms(lambda: pm.ntt(da_, db_, out=c_), 7, flush, stream)
+        t_plain = None
+        if logn <= 18:
+            pm.plain(da_, db_, s=8, out=c_)
+            t_plain = median_ms(lambda: pm.plain(da_, db_, s=8, out=c_), 5 if logn <= 16 else 3, flush, stream)
+        sweep.append({"deg": n_ - 1, "ms_ntt": t_ntt, "ms_plain_s8": t_plain})
+    cross = next((r["deg"] for r in sweep if r["ms_plain_s8"] is not None and r["ms_ntt"] < r["ms_plain_s8"]), None)
+    rows["ntt_crossover"] = {"points": sweep, "first_deg_where_ntt_wins": cross}
     return rows
 
 

@@ -1,0 +1,106 @@
+"""Parity of the tensor-core batched form (bf16 limbs, fp32 accumulation) with the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_0264_gb300 import inputs
+from paper_1402_0264_gb300 import polymul as pm
+from tests.gpuhelp import assert_equal, dev, dev64, host
+
+pytestmark = pytest.mark.gpu
+P = inputs.P_DEFAULT
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_0264_gb300 import build
+    build.build()
+
+
+def run(packed, max_deg, p=P, mode=pm.PM_TENSOR):
+    a_data, a_off, b_data, b_off, c_off = packed
+    out = pm.batched(dev(a_data), dev64(a_off), dev(b_data), dev64(b_off), dev64(c_off),
+                     max_deg=max_deg, p=p, mode=mode, total=int(c_off[-1]))
+    assert pm.sync_status() == 0
+    return host(out)
+
+
+def test_small_ragged_batch():
+    da = np.array([0, 1, 5, 31, 32, 33, 1000, 1535, 1536, 2047, 4095, 17], np.int64)
+    db = np.array([0, 3, 5, 32, 31, 33, 17, 1536, 1535, 2047, 4095, 4000], np.int64)
+    packed = inputs.packed_batch(da, db, 91)
+    assert_equal(run(packed, 4095), oracle.polymul_batch(*packed[:4], packed[4], P))
+
+
+@pytest.mark.parametrize("deg", [63, 1535, 3071, 4095])
+def test_equal_degrees(deg):
+    packed = inputs.workload_tensor(batch=16, deg=deg, seed=inputs.SEED_BASE + 300 + deg)
+    assert_equal(run(packed, deg), oracle.polymul_batch(*packed[:4], packed[4], P), f"deg {deg}")
+
+
+def _adversarial_values(p):
+    """Coefficients whose balanced digits are all at the extreme (-128 for b, -32 for a)."""
+    xb = p - 128 * (1 + 256 + 65536)        # digits (-128, -128, -128, 0) in base 256
+    xa = p - 32 * (1 + 64 + 4096 + 262144)  # digits (-32, -32, -32, -32, 0) in base 64
+    return xa, xb
+
+
+def test_worst_case_accumulation():
+    """Every product of digits is 4096 and 4096 terms meet: sums reach 2^24 exactly."""
+    xa, xb = _adversarial_values(P)
+    n = m = 4096
+    a = np.full(n, xa, np.uint32)
+    b = np.full(m, xb, np.uint32)
+    a_off = np.array([0, n], np.int64); b_off = np.array([0, m], np.int64)
+    c_off = np.array([0, n + m - 1], np.int64)
+    packed = (a, a_off, b, b_off, c_off)
+    want = oracle.polymul(a, b, P)
+    assert_equal(run(packed, 4095), want, "adversarial digits")
+    # both operand orders, and all p-1
+    assert_equal(run((b, b_off, a, a_off, c_off), 4095), want, "swapped")
+    ones = np.full(n, P - 1, np.uint32)
+    assert_equal(run((ones, a_off, ones, b_off, c_off), 4095), oracle.polymul(ones, ones, P), "p-1")
+
+
+def test_tensor_workload_full():
+    """1024 pairs of degree 4095 against the transform oracle, plus the plain path."""
+    packed = inputs.workload_tensor()
+    got = run(packed, 4095)
+    want = oracle.ntt_polymul_batch(*packed[:4], packed[4], P)
+    assert_equal(got, want, "1024 x deg 4095")
+    # a sample of pairs by the definition
+    a_data, a_off, b_data, b_off, c_off = packed
+    for i in (0, 511, 1023):
+        a = a_data[a_off[i]:a_off[i + 1]]; b = b_data[b_off[i]:b_off[i + 1]]
+        assert_equal(got[c_off[i]:c_off[i + 1]], oracle.polymul(a, b, P), f"pair {i}")
+
+
+def test_matches_plain_batched_and_auto_mode():
+    packed = inputs.workload_batched(batch=300)
+    da = packed[1][1:] - packed[1][:-1]
+    assert da.max() <= 2049
+    t = run(packed, 2048, mode=pm.PM_TENSOR)
+    pl = run(packed, 2048, mode=pm.PM_PLAIN)
+    au = run(packed, 2048, mode=pm.PM_AUTO)
+    assert_equal(t, pl, "tensor vs plain")
+    assert_equal(au, pl, "auto vs plain")
+
+
+def test_other_modulus():
+    p = 65537
+    packed = inputs.packed_batch(np.array([100, 4095]), np.array([4095, 3000]), 5, p)
+    assert_equal(run(packed, 4095, p=p), oracle.polymul_batch(*packed[:4], packed[4], p))
+
+
+def test_bad_offsets_and_degrees():
+    import torch
+    da = np.array([10, 5000], np.int64)
+    packed = inputs.packed_batch(da, da, 3)
+    out = torch.full((int(packed[4][-1]),), 7, dtype=torch.uint32, device="cuda")
+    pm.batched(dev(packed[0]), dev64(packed[1]), dev(packed[2]), dev64(packed[3]), dev64(packed[4]),
+               max_deg=4095, mode=pm.PM_TENSOR, out=out, total=out.numel())
+    assert pm.sync_status() == 1   # a degree above max_deg is refused on the device
+    assert (host(out) == 7).all()
