@@ -431,6 +431,46 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
                              "macs_per_s": macs / (ms_g * 1e-3), "products_per_s": 4096 / (ms_g * 1e-3),
                              "alu_frac": macs / (ms_g * 1e-3) / alu_peak_macs()}
 
+    # --- tensor-core form: 1024 pairs of degree 4095 (and the plain form on the same batch) ---
+    tp = inputs.workload_tensor()
+    macs_t = int(((tp[1][1:] - tp[1][:-1]) * (tp[3][1:] - tp[3][:-1])).sum())
+    tt = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in tp]
+    outt = torch.empty(int(tp[4][-1]), dtype=torch.uint32, device=dev)
+    run_t = lambda: pm.batched(tt[0], tt[1], tt[2], tt[3], tt[4], max_deg=4095, mode=pm.PM_TENSOR,
+                               out=outt, total=outt.numel())
+    run_t()
+    ms_t = median_ms(run_t, 10, flush, stream)
+    want_t = oracle.ntt_polymul_batch(*tp[:4], tp[4], P)
+    assert np.array_equal(outt.cpu().numpy().view(np.uint32), want_t)
+    run_tp = lambda: pm.batched(tt[0], tt[1], tt[2], tt[3], tt[4], max_deg=4095, mode=pm.PM_PLAIN, s=8,
+                                out=outt, total=outt.numel())
+    run_tp()
+    ms_tp = median_ms(run_tp, 5, flush, stream)
+    assert np.array_equal(outt.cpu().numpy().view(np.uint32), want_t)
+    # tensor work actually issued: per tile (1536 outputs) and shift, 2 MMAs of 128 x 240 x 16
+    tflops_issued = None
+    try:
+        nt = 0
+        for i in range(len(tp[1]) - 1):
+            n_ = int(tp[1][i + 1] - tp[1][i]); m_ = int(tp[3][i + 1] - tp[3][i])
+            if m_ > n_:
+                n_, m_ = m_, n_
+            NA = (n_ + 31) // 32; dmax = (m_ + 30) // 32
+            for t_ in range((n_ + m_ - 1 + 1535) // 1536):
+                I0 = 48 * t_
+                nt += min(dmax, I0 + 47) - max(0, I0 - NA + 1) + 1
+        tflops_issued = nt * 2 * 2 * 128 * 240 * 16 / (ms_t * 1e-3) / 1e12
+    except Exception:
+        pass
+    rows["tensor_batched"] = {"workload": "1024 pairs of degree 4095", "macs": macs_t, "ms": ms_t,
+                              "macs_per_s": macs_t / (ms_t * 1e-3), "products_per_s": 1024 / (ms_t * 1e-3),
+                              "plain_s8_ms_same_batch": ms_tp,
+                              "plain_s8_macs_per_s": macs_t / (ms_tp * 1e-3),
+                              "speedup_vs_plain": ms_tp / ms_t,
+                              "bf16_tflops_issued": tflops_issued,
+                              "tensor_frac_of_measured_bf16": (tflops_issued / pk["bf16_tflops"]
+                                                               if tflops_issued else None)}
+
     # --- transform path: one pair of degree 2^22 - 1, and the plain/transform crossover ---
     an, bn = inputs.workload_ntt()
     dan, dbn = torch.from_numpy(an).to(dev), torch.from_numpy(bn).to(dev)
