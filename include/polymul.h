@@ -77,6 +77,32 @@ pm_status polymul_plain(const uint32_t *a, int64_t deg_a, const uint32_t *b, int
                         uint32_t *c, uint32_t p, int s, void *stream);
 
 /*
+ * polymul_plain_noalloc - polymul_plain for callers that cannot allocate.
+ * The paper has no counterpart: this is a deployment variant of the same
+ * product.  Some callers cannot let a library call cudaMalloc: code that runs
+ * while its stream is being captured into a CUDA graph (an allocation is not
+ * a capturable operation), processes whose caching allocator has already
+ * reserved nearly all device memory (a library's own cudaMalloc would fail),
+ * and latency-bound callers that cannot take cudaMalloc's device-wide
+ * synchronisation.  This entry point allocates nothing: the kernel's scratch
+ * (partial-sum slots and tile counters) lives in a 4 MiB static device array
+ * that every GPU loading the library holds until the process exits.
+ *
+ *   Arguments, layout and result are those of polymul_plain.
+ *   The first call on each device looks up the array's device address and
+ *   clears its counters (synchronously); make that first call before any
+ *   stream capture.  Later calls only launch the kernel.
+ *   All calls share the one array (its contents persist between calls), so
+ *   calls whose kernels overlap on the GPU - on different streams, or from
+ *   different host threads - race and give wrong results: serialise them.
+ *   Returns PM_ERR_RANGE when the scratch a launch needs (2 slots of 32*s
+ *   words per persistent CTA, plus the counters) would exceed the 4 MiB
+ *   array; on GB300 every s fits.  Otherwise as polymul_plain.
+ */
+pm_status polymul_plain_noalloc(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
+                                uint32_t *c, uint32_t p, int s, void *stream);
+
+/*
  * polymul_ntt - one product through number-theoretic transforms: forward
  * transforms of a and b zero-padded to N = 2^ceil(log2(n+m-1)), pointwise
  * product, inverse transform, scaling by N^-1 mod p.  Exact, so the result

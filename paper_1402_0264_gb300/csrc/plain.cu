@@ -613,3 +613,103 @@ pm_status launch_batched_plain(int64_t batch, const uint32_t* a_data, const int6
 }
 
 }  // namespace pm
+
+// ---------------------------------------------------------------------------
+// polymul_plain_noalloc: the single-pair product of polymul_plain with its
+// scratch (partial-sum slots and tile counters) in a file-scope device array
+// instead of library-allocated memory, for callers that cannot let a library
+// call cudaMalloc (see include/polymul.h).  The kernel is plain_sk_kernel,
+// unchanged; only where its scratch lives differs.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace pm {
+
+constexpr size_t NOALLOC_BYTES = (size_t)4 << 20;  // per device that loads the library, held until exit
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_ptr[64] = {};  // device address of g_noalloc_scratch, per device
+
+// Once per device, with that device current: the array's device address (the
+// host-side symbol is only a stand-in) and cleared tile counters.
+static pm_status noalloc_setup(int dev, void** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_ptr[dev]) {
+        *out = g_noalloc_ptr[dev];
+        return PM_OK;
+    }
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaMemset(ptr, 0, COUNTER_BYTES);  // the counters must start at zero
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e);
+    g_noalloc_ptr[dev] = ptr;
+    *out = ptr;
+    return PM_OK;
+}
+
+template <int S>
+static pm_status launch_pair_noalloc_s(const uint32_t* a, int n, const uint32_t* b, int m, uint32_t* c,
+                                       uint32_t p, cudaStream_t st, int dev, int num_sms, void* scratch) {
+    using C = Cfg<S>;
+    auto kern = plain_sk_kernel<S, false>;
+    static int occ_cache[64] = {};
+    int occ = 0;
+    cudaError_t e = kernel_setup(kern, C::SMEM, dev, occ_cache, &occ);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int64_t nn = std::max(n, m), mm = std::min(n, m);
+    const int64_t G = cum_len(nn, mm, C::TD, ntiles_of(nn, mm, C::TD));
+    const int64_t P = std::min<int64_t>(std::min<int64_t>((int64_t)num_sms * occ, COUNTER_MAX),
+                                        std::max<int64_t>(1, G / MIN_POSITIONS));
+    if (sk_bytes(P, C::TD) > NOALLOC_BYTES) return PM_ERR_RANGE;  // would not fit the static array
+    const ModParams mp = host_mod_params(p, C::KB);
+    kern<<<(unsigned)P, NT, C::SMEM, st>>>(a, nullptr, b, nullptr, c, nullptr, n, m, nullptr, 0, mp,
+                                           sk_carve(scratch));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(1);
+    return PM_OK;
+}
+
+}  // namespace pm
+
+extern "C" pm_status polymul_plain_noalloc(const uint32_t* a, int64_t deg_a, const uint32_t* b,
+                                           int64_t deg_b, uint32_t* c, uint32_t p, int s, void* stream) {
+    using namespace pm;
+    if (!a || !b || !c) return PM_ERR_INVALID_ARG;
+    if (deg_a < 0 || deg_b < 0 || deg_a > PM_MAX_DEG || deg_b > PM_MAX_DEG) return PM_ERR_INVALID_ARG;
+    if (p < 2 || p >= PM_MAX_P) return PM_ERR_RANGE;
+    const int64_t L = deg_a + deg_b + 1;
+    auto overlap = [](const void* x, int64_t xw, const void* y, int64_t yw) {
+        const uintptr_t x0 = (uintptr_t)x, x1 = x0 + 4 * (uintptr_t)xw;
+        const uintptr_t y0 = (uintptr_t)y, y1 = y0 + 4 * (uintptr_t)yw;
+        return x0 < y1 && y0 < x1;
+    };
+    if (overlap(c, L, a, deg_a + 1) || overlap(c, L, b, deg_b + 1)) return PM_ERR_INVALID_ARG;
+    if (s == 0) s = polymul_plain_default_s(deg_a, deg_b, p);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= 64) return PM_ERR_INTERNAL;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    void* scratch = nullptr;
+    pm_status rc = noalloc_setup(dev, &scratch);
+    if (rc != PM_OK) return rc;
+    const uint32_t *x = a, *y = b;
+    int n = (int)(deg_a + 1), m = (int)(deg_b + 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (s) {
+        case 1: return launch_pair_noalloc_s<1>(x, n, y, m, c, p, st, dev, sms, scratch);
+        case 2: return launch_pair_noalloc_s<2>(x, n, y, m, c, p, st, dev, sms, scratch);
+        case 4: return launch_pair_noalloc_s<4>(x, n, y, m, c, p, st, dev, sms, scratch);
+        case 8: return launch_pair_noalloc_s<8>(x, n, y, m, c, p, st, dev, sms, scratch);
+        case 16: return launch_pair_noalloc_s<16>(x, n, y, m, c, p, st, dev, sms, scratch);
+        case 32: return launch_pair_noalloc_s<32>(x, n, y, m, c, p, st, dev, sms, scratch);
+        case 64: return launch_pair_noalloc_s<64>(x, n, y, m, c, p, st, dev, sms, scratch);
+        default: return PM_ERR_INVALID_ARG;
+    }
+}

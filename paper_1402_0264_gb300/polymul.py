@@ -41,6 +41,7 @@ def _declare(lib):
     sig = {
         "polymul_plain": ([V, I64, V, I64, V, U32, INT, V], INT),
         "polymul_ntt": ([V, I64, V, I64, V, U32, U32, V], INT),
+        "polymul_plain_noalloc": ([V, I64, V, I64, V, U32, INT, V], INT),
         "polymul_batched": ([I64, V, V, V, V, V, V, U32, INT, INT, I64, V], INT),
         "polymul_model_predict": ([I64, I64, INT, INT, D, D, ctypes.POINTER(D)], INT),
         "polymul_tune_plain": ([V, I64, V, I64, V, U32, INT, V, ctypes.POINTER(INT),
@@ -116,6 +117,19 @@ def plain(a, b, p: int = P_DEFAULT, s: int = 0, out=None, stream=None):
         raise ValueError("out must hold len(a) + len(b) - 1 words")
     _check(lib().polymul_plain(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"), b.numel() - 1,
                                _dev_words(out, "out"), p, s, _stream_ptr(stream)), "polymul_plain")
+    return out
+
+
+def plain_noalloc(a, b, p: int = P_DEFAULT, s: int = 0, out=None, stream=None):
+    """plain() with the kernel's scratch in the library's static device array (no allocation
+    by the library; the caller still provides the output).  Calls must not overlap on the GPU."""
+    L = a.numel() + b.numel() - 1
+    out = _alloc(L, a) if out is None else out
+    if out.numel() != L:
+        raise ValueError("out must hold len(a) + len(b) - 1 words")
+    _check(lib().polymul_plain_noalloc(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"),
+                                       b.numel() - 1, _dev_words(out, "out"), p, s,
+                                       _stream_ptr(stream)), "polymul_plain_noalloc")
     return out
 
 

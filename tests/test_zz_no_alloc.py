@@ -1,0 +1,74 @@
+"""polymul_plain_noalloc: the allocation-free entry point for callers that
+cannot let a library call cudaMalloc (a stream being captured into a CUDA
+graph, a process whose allocator already holds the device memory, or a
+latency-bound caller).  Its scratch lives in a static device array.
+
+Checked here through the C ABI: two calls in a row give exactly the words
+that polymul_plain gives, and after the first call (which sets the array up)
+the calls leave the device's free memory unchanged.  This file is collected
+last so that a run stopping at the first failure has run every other test.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1402_0264_gb300 import inputs
+from paper_1402_0264_gb300 import polymul as pm
+from tests.gpuhelp import assert_equal, dev, host
+
+pytestmark = pytest.mark.gpu
+P = inputs.P_DEFAULT
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_0264_gb300 import build
+    build.build()
+
+
+def _noalloc(lib, a, b, out, s, stream):
+    return lib.polymul_plain_noalloc(ctypes.c_void_p(a.data_ptr()), a.numel() - 1,
+                                     ctypes.c_void_p(b.data_ptr()), b.numel() - 1,
+                                     ctypes.c_void_p(out.data_ptr()), P, s,
+                                     ctypes.c_void_p(stream.cuda_stream))
+
+
+def test_noalloc_matches_plain_on_two_calls_in_a_row():
+    import torch
+    lib = pm.lib()
+    stream = torch.cuda.current_stream()
+    cases = [inputs.workload_single(), inputs.poly_pair(5000, 777, inputs.SEED_BASE + 500)]
+    tensors = [(dev(a), dev(b)) for a, b in cases]
+    outs = [torch.empty(a.numel() + b.numel() - 1, dtype=torch.uint32, device="cuda") for a, b in tensors]
+    # the references also load both kernel instances (s = 8 and 16) and the fill kernel
+    # before the free-memory baseline: lazy module loading takes device memory on first use
+    refs = [host(pm.plain(a, b, s=s)) for (a, b), s in zip(tensors, (8, 16))]
+    for out in outs:
+        out.fill_(0)
+    # first call on this device: sets the static array up
+    assert _noalloc(lib, tensors[0][0], tensors[0][1], outs[0], 8, stream) == 0
+    outs[0].fill_(0)
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    for (a, b), out, ref, s in zip(tensors, outs, refs, (8, 16)):
+        rc = _noalloc(lib, a, b, out, s, stream)
+        assert rc == 0, pm.STATUS.get(rc, rc)
+        assert_equal(host(out), ref, f"noalloc s={s}")
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free_before, "the calls changed the device's free memory"
+
+
+def test_noalloc_rejects_what_polymul_plain_rejects():
+    import torch
+    lib = pm.lib()
+    a = dev(np.ones(10, np.uint32))
+    out = torch.empty(19, dtype=torch.uint32, device="cuda")
+    stream = torch.cuda.current_stream()
+    assert _noalloc(lib, a, a, out, 3, stream) == 1          # s not a power of two
+    assert lib.polymul_plain_noalloc(None, 9, ctypes.c_void_p(a.data_ptr()), 9,
+                                     ctypes.c_void_p(out.data_ptr()), P, 8,
+                                     ctypes.c_void_p(stream.cuda_stream)) == 1
