@@ -70,7 +70,7 @@ def source_hash(*names):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, src: str):
+def traffic_for(kernel: str, *src: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
@@ -78,7 +78,7 @@ def traffic_for(kernel: str, src: str):
     except OSError:
         return None
     ent = t.get(kernel)
-    if not ent or ent.get("source_sha") != source_hash(src):
+    if not ent or ent.get("source_sha") != source_hash(*src):
         return None
     return ent.get("bytes_per_launch")
 
@@ -308,7 +308,7 @@ def run_ours(args, world, rank, local):
         return 0
 
     pk, pk_kind = peaks()
-    kern_name = f"plain_pair_kernel<{s}>"
+    kern_name = f"plain_sk_kernel<{s}>"
     achieved = MACS_SINGLE / (ms_per_step * 1e-3)
     peak = alu_peak_macs()
     line = {
@@ -325,7 +325,7 @@ def run_ours(args, world, rank, local):
                      "frac_at_sampled_clock": (achieved / alu_peak_macs(clocks["sm_mhz"])
                                                if clocks.get("sm_mhz") else None),
                      "kernel": kern_name,
-                     "traffic": traffic_for(f"plain_pair_kernel<{s}>", "plain.cu")},
+                     "traffic": traffic_for(f"plain_sk_kernel<{s}>", "plain.cu", "common.cuh")},
         "e2e": {"value": world * MACS_SINGLE * K / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(a_h.numel() * 4 + b_h.numel() * 4),
                 "d2h_bytes_per_step": int(c_h.numel() * 4)},
@@ -504,6 +504,68 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
     return rows
 
 
+def run_case(args):
+    """One kernel family on its workload: W warm-up and K timed steps (CUDA events, L2 flushed)."""
+    import torch
+
+    import oracle
+    from paper_1402_0264_gb300 import build as pbuild
+    from paper_1402_0264_gb300 import polymul as pm
+
+    if not os.path.exists(pm.LIB_PATH):
+        pbuild.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush_buf = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    s = args.s or 8
+    if args.case == "plain":
+        a, b = inputs.workload_single()
+        ta, tb = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+        out = torch.empty(len(a) + len(b) - 1, dtype=torch.uint32, device=dev)
+        step = lambda: pm.plain(ta, tb, s=s, out=out)
+        want = lambda: oracle.polymul(a, b, P)
+        macs, name = len(a) * len(b), "degree-16383 pair, plain s=%d" % s
+    elif args.case == "ntt":
+        a, b = inputs.workload_ntt()
+        ta, tb = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
+        out = torch.empty(len(a) + len(b) - 1, dtype=torch.uint32, device=dev)
+        step = lambda: pm.ntt(ta, tb, out=out)
+        want = lambda: oracle.ntt_polymul(a, b, P)
+        macs, name = len(a) * len(b), "degree 2^22-1 pair, transform"
+    else:
+        packed = inputs.workload_batched() if args.case == "batched" else inputs.workload_tensor()
+        max_deg = 2048 if args.case == "batched" else 4095
+        mode = pm.PM_PLAIN if args.case == "batched" else pm.PM_TENSOR
+        t = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in packed]
+        out = torch.empty(int(packed[4][-1]), dtype=torch.uint32, device=dev)
+        step = lambda: pm.batched(t[0], t[1], t[2], t[3], t[4], max_deg=max_deg, mode=mode, s=s,
+                                  out=out, total=out.numel())
+        want = (lambda: oracle.polymul_batch(*packed[:4], packed[4], P)) if args.case == "batched" else \
+               (lambda: oracle.ntt_polymul_batch(*packed[:4], packed[4], P))
+        macs = int(((packed[1][1:] - packed[1][:-1]) * (packed[3][1:] - packed[3][:-1])).sum())
+        name = ("4096 pairs, degrees log-uniform in [16,2048], plain s=%d" % s if args.case == "batched"
+                else "1024 pairs of degree 4095, tensor cores")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), want()), "result differs from the oracle"
+    ts = []
+    for _ in range(args.steps):
+        flush_buf.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    assert pm.sync_status() == 0
+    ms = sum(ts) / len(ts)
+    print(json.dumps({"case": args.case, "workload": name, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "macs_per_s": macs / (ms * 1e-3), "unit": UNIT}), flush=True)
+    return 0
+
+
 def cpu_baseline(a_np, b_np):
     import oracle
     oracle.polymul(a_np[:8], b_np[:8], P)
@@ -528,12 +590,16 @@ def main():
     ap.add_argument("--no-rows", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--s", type=int, default=0, help="fix the block parameter (skip the tuner)")
+    ap.add_argument("--case", choices=["plain", "batched", "tensor", "ntt"], default=None,
+                    help="time one kernel family alone (profiling runs); prints one JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         rc = run_reference(args, world, rank)
+    elif args.case:
+        rc = run_case(args)
     else:
         rc = run_ours(args, world, rank, local)
     if world > 1:

@@ -110,9 +110,11 @@ pm_status polymul_plain_noalloc(const uint32_t *a, int64_t deg_a, const uint32_t
  * this is the large-degree path of the same product.)
  *
  *   p must be prime with N | p-1 and g a generator of (Z/pZ)^*; pass g = 0
- *   for p = 469762049 (7*2^26+1, generator 3).  N <= 2^26.
- * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_UNSUPPORTED (N does not divide
- * p-1, or no generator known), PM_ERR_NOMEM (twiddle tables) or PM_ERR_CUDA.
+ *   for p = 469762049 (7*2^26+1, generator 3).  N <= 2^24 (n+m-1 <= 2^24).
+ *   Uses 8N bytes of library scratch per (device, stream) for N > 4096.
+ * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_RANGE (N > 2^24),
+ * PM_ERR_UNSUPPORTED (N does not divide p-1, no generator known, or g has
+ * the wrong order), PM_ERR_NOMEM (tables, scratch) or PM_ERR_CUDA.
  */
 pm_status polymul_ntt(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
                       uint32_t *c, uint32_t p, uint32_t g, void *stream);
