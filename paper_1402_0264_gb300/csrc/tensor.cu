@@ -15,22 +15,30 @@
 // (tcgen05 kind::i8 would hold larger limbs, but ptxas rejects it for
 // sm_103a.)
 //
-// Matrix form (T = 32 outputs per block, block I covers outputs 32 I .. 32 I + 31):
-//     D[(j, r)][(I, i)] = sum_delta sum_{k<32} d_j[32 delta + r - k] * e_i[32 (I - delta) + k]
+// Matrix form (T = 32 outputs per block, block I covers outputs 32 I .. 32 I + 31;
+// the K index runs backwards, k' = 31 - k, in both operands):
+//     D[(j, r)][(I, i)] = sum_delta sum_{k'<32} d_j[32 delta - 31 + r + k'] * e_i[32 (I - delta) + 31 - k']
 //                       = (e_i * d_j)[32 I + r].
-// For one shift delta this is one 128 x 240 x 32 product: M = 128 rows are
-// the 4 limbs of b times 32 offsets r (a Toeplitz block of b, rebuilt in
-// shared memory per delta), N = 240 columns are 48 output blocks times the 5
-// limbs of a, K = 32.  The a operand is stored once per tile as rows (J, i) =
-// limb i of block J of a; the rows the product needs for shift delta are the
-// same rows moved by 5 (48 blocks) positions per delta, so its shared-memory
-// descriptor just starts 5 * 16 bytes earlier for each delta.  All shifts
-// accumulate into one TMEM tile (240 fp32 columns x 128 lanes).
+// For one shift delta this is one 128 x 240 x 32 product (two MMAs of K = 16):
+// N = 240 columns are 48 output blocks times the 5 limbs of a; the a operand
+// is stored once per tile as rows (J, i) = limb i of block J of a, reversed,
+// and the rows shift delta needs are the same rows moved by 5 per delta, so
+// its descriptor just starts 5 * 16 bytes earlier for each delta.  M = 128
+// rows are the 4 limbs of b times 32 offsets r, ordered (r / 8, limb j, r mod 8)
+// so that one descriptor covers all limbs: with k' reversed, the 8 x 8 core
+// matrix of limb j at row group r / 8 = g and K chunk c holds
+// d_j[32 delta - 31 + 8 (g + c) + row + column], a Hankel block that depends
+// only on q = 4 delta + g + c.  These core matrices H_j[q] are built once per
+// q in shared memory, the 4 limbs interleaved (512 bytes per q), and the
+// descriptor walks them with 128 bytes between row groups (the next limb or,
+// after 4 limbs, the next g) and 512 bytes between K chunks (the next q).  A
+// shift thus costs 4 new core matrices per limb instead of a 128 x 32 block.
+// All shifts accumulate into one TMEM tile (240 fp32 columns x 128 lanes).
 //
-// Epilogue.  Warp j reads TMEM lanes 32 j .. 32 j + 31 (limb j of b): lane r
-// holds D[(j, r)][(I, i)] for every I and i; it forms sum_i 64^i D (exact in
-// int64), reduces it mod p, multiplies by 256^j mod p, and the four limbs are
-// added through shared memory before the 1536 outputs of the tile are stored.
+// Epilogue.  TMEM lane 32 g + 8 j + t holds D[(j, 8 g + t)][.]: warp g reads
+// its 32 lanes, each thread forms sum_i 64^i D (exact in int64), reduces it
+// mod p and multiplies by 256^j mod p, and the 4 limbs of one output are
+// added with two warp shuffles before the store.
 //
 // Work: tiles of 1536 outputs of every pair, taken by persistent CTAs (one
 // per SM) from an atomic counter.  Every wait on an mbarrier is bounded: when
@@ -50,22 +58,21 @@ constexpr int MMA_M = 128, MMA_N = NBLK * NA_LIMB;  // 240
 constexpr int TILE_OUT = TT * NBLK;        // 1536
 constexpr int TC_MAXK = 4096;              // exactness bound on min(n, m)
 constexpr int TC_THREADS = 256;
-constexpr int GROUP_D = 4;                 // shifts per A-operand group (two groups in flight)
+constexpr int GROUP_D = 8;                 // shifts per A-operand group (two groups in flight)
 constexpr int MAX_DELTA = TC_MAXK / TT + 2;            // shifts a tile can need
 constexpr int BD_LEN = TT * (MAX_DELTA + 2);           // b digits staged per limb
 constexpr int ROWS_MAX = NA_LIMB * (NBLK + MAX_DELTA + 2);
 constexpr int B_LBO = ROWS_MAX * 16;                   // bytes between K chunks of the a operand
-constexpr int A_STAGE = MMA_M * 4 * 16;                // 8 KB: 128 rows x 32 bf16
-constexpr int A_LBO = MMA_M * 16;                      // 2 KB
+constexpr int H_Q = 4 * GROUP_D + 4;                  // Hankel core-matrix indices per group (4 G + 3 used)
+constexpr int H_SLOT = H_Q * 512;                      // 4 limbs x 128-byte core matrices per index
 constexpr uint32_t TMEM_COLS = 256;
 constexpr int64_t WAIT_LIMIT = 1ll << 26;              // polls before a wait is declared lost
 
 // shared memory map (bytes)
 constexpr int SM_B = 0;                                   // a operand: 4 chunks x ROWS_MAX rows
-constexpr int SM_A = SM_B + 4 * B_LBO;                    // 2 groups x GROUP_D stages
-constexpr int SM_BD = SM_A + 2 * GROUP_D * A_STAGE;       // b digits: NB_LIMB x BD_LEN bf16
-constexpr int SM_RED = SM_BD + NB_LIMB * BD_LEN * 2;      // epilogue: NB_LIMB x TILE_OUT u32
-constexpr int SM_CTL = SM_RED + NB_LIMB * TILE_OUT * 4;   // mbarriers, TMEM address, tile id
+constexpr int SM_H = SM_B + 4 * B_LBO;                    // 2 groups of Hankel core matrices
+constexpr int SM_BD = SM_H + 2 * H_SLOT;                  // b digits: NB_LIMB x BD_LEN bf16
+constexpr int SM_CTL = SM_BD + NB_LIMB * BD_LEN * 2;      // mbarriers, TMEM address, tile id
 constexpr int TC_SMEM = SM_CTL + 128;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -137,9 +144,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     unsigned int* __restrict__ counter, TcParams tp, int* status) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint8_t* sB = sm + SM_B;
-    uint8_t* sA = sm + SM_A;
+    uint8_t* sH = sm + SM_H;
     uint16_t* sbd = reinterpret_cast<uint16_t*>(sm + SM_BD);
-    uint32_t* sred = reinterpret_cast<uint32_t*>(sm + SM_RED);
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + SM_CTL);  // 2 mbarriers
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + SM_CTL + 32);
     int* s_tile = reinterpret_cast<int*>(sm + SM_CTL + 48);
@@ -215,8 +221,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
 #pragma unroll
             for (int i = 0; i < NA_LIMB; ++i) {
                 const int d = ((v + 32) & 63) - 32;
-                const int row = NA_LIMB * Jr + i;
-                *reinterpret_cast<uint16_t*>(sB + (k >> 3) * B_LBO + row * 16 + (k & 7) * 2) = bf16_bits(d);
+                const int row = NA_LIMB * Jr + i, kr = TT - 1 - k;  // K runs backwards
+                *reinterpret_cast<uint16_t*>(sB + (kr >> 3) * B_LBO + row * 16 + (kr & 7) * 2) = bf16_bits(d);
                 v = (v - d) >> 6;
             }
         }
@@ -236,34 +242,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             }
             __syncthreads();
             if (*s_abort) break;
-            uint8_t* stage0 = sA + buf * GROUP_D * A_STAGE;
+            uint8_t* hslot = sH + buf * H_SLOT;
             const int nds = min(GROUP_D, nd - gi * GROUP_D);
-            // chunk (s, row, kc): 8 elements k = 8 kc .. 8 kc + 7 of row (j, r) for shift d
-            for (int q = tid; q < nds * MMA_M * 4; q += TC_THREADS) {
-                const int s = q / (MMA_M * 4), rem = q % (MMA_M * 4);
-                const int kc = rem / MMA_M, row = rem % MMA_M;
-                const int j = row >> 5, r = row & 31;
-                const int d = d_lo + gi * GROUP_D + s;
-                const int base = TT * d + r - 8 * kc - tb0;  // staged index of k = 8 kc
-                const uint16_t* src = sbd + j * BD_LEN;
+            const int dg = d_lo + gi * GROUP_D;  // first shift of the group
+            // row t of H_j[q] (q = 4 dg + qq) holds d_j[-31 + 8 q + t .. + 7], 8 ascending digits
+            for (int w = tid; w < (4 * nds + 3) * NB_LIMB * 8; w += TC_THREADS) {
+                const int qq = w >> 5, j = (w >> 3) & 3, t = w & 7;
+                const int base = -31 + 8 * (4 * dg + qq) + t - tb0;  // staged index of the first digit
+                const uint16_t* src = sbd + j * BD_LEN + base;
                 uint4 v;
-                v.x = (uint32_t)src[base] | ((uint32_t)src[base - 1] << 16);
-                v.y = (uint32_t)src[base - 2] | ((uint32_t)src[base - 3] << 16);
-                v.z = (uint32_t)src[base - 4] | ((uint32_t)src[base - 5] << 16);
-                v.w = (uint32_t)src[base - 6] | ((uint32_t)src[base - 7] << 16);
-                *reinterpret_cast<uint4*>(stage0 + s * A_STAGE + kc * A_LBO + row * 16) = v;
+                v.x = (uint32_t)src[0] | ((uint32_t)src[1] << 16);
+                v.y = (uint32_t)src[2] | ((uint32_t)src[3] << 16);
+                v.z = (uint32_t)src[4] | ((uint32_t)src[5] << 16);
+                v.w = (uint32_t)src[6] | ((uint32_t)src[7] << 16);
+                *reinterpret_cast<uint4*>(hslot + qq * 512 + j * 128 + t * 16) = v;
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int s = 0; s < nds; ++s) {
-                    const int d = d_lo + gi * GROUP_D + s;
-                    const uint32_t a_addr = smem_u32(stage0 + s * A_STAGE);
+                    const int d = dg + s;
                     const uint32_t b_addr = smem_u32(sB) + (uint32_t)(NA_LIMB * (d_hi - d) * 16);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const uint64_t da = smem_desc(a_addr + 2 * h * A_LBO, A_LBO, 128);
+                        const uint64_t da = smem_desc(smem_u32(hslot) + (uint32_t)((4 * s + 2 * h) * 512), 512, 128);
                         const uint64_t db = smem_desc(b_addr + 2 * h * B_LBO, B_LBO, 128);
                         mma_bf16(tmem, da, db, (gi == 0 && s == 0 && h == 0) ? 0u : 1u);
                     }
@@ -284,46 +287,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
         __syncthreads();
         if (*s_abort) break;
 
-        // ---- epilogue: warp j reads limb j of b (TMEM lanes 32 j ..) ----
-        if (warp < NB_LIMB) {
+        // ---- epilogue: warp g reads TMEM lanes 32 g .. 32 g + 31 = (limb j, offset 8 g + t) ----
+        if (warp < 4) {
             const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-            const uint64_t wj = tp.w256[warp];
+            const int j = lane >> 3, r = 8 * warp + (lane & 7);
+            const uint64_t wj = tp.w256[j];
             for (int c0 = 0; c0 < MMA_N; c0 += 80) {  // 16 blocks x 5 limbs per round
-                uint32_t r[80];
+                uint32_t rr[80];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
                         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(r[16 * q + 0]), "=r"(r[16 * q + 1]), "=r"(r[16 * q + 2]), "=r"(r[16 * q + 3]),
-                          "=r"(r[16 * q + 4]), "=r"(r[16 * q + 5]), "=r"(r[16 * q + 6]), "=r"(r[16 * q + 7]),
-                          "=r"(r[16 * q + 8]), "=r"(r[16 * q + 9]), "=r"(r[16 * q + 10]), "=r"(r[16 * q + 11]),
-                          "=r"(r[16 * q + 12]), "=r"(r[16 * q + 13]), "=r"(r[16 * q + 14]), "=r"(r[16 * q + 15])
+                        : "=r"(rr[16 * q + 0]), "=r"(rr[16 * q + 1]), "=r"(rr[16 * q + 2]), "=r"(rr[16 * q + 3]),
+                          "=r"(rr[16 * q + 4]), "=r"(rr[16 * q + 5]), "=r"(rr[16 * q + 6]), "=r"(rr[16 * q + 7]),
+                          "=r"(rr[16 * q + 8]), "=r"(rr[16 * q + 9]), "=r"(rr[16 * q + 10]), "=r"(rr[16 * q + 11]),
+                          "=r"(rr[16 * q + 12]), "=r"(rr[16 * q + 13]), "=r"(rr[16 * q + 14]), "=r"(rr[16 * q + 15])
                         : "r"(tmem + lane_base + (uint32_t)(c0 + 16 * q)));
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int ib = 0; ib < 16; ++ib) {
-                    int64_t s = 0;
+                    int64_t sum = 0;
 #pragma unroll
                     for (int i = NA_LIMB - 1; i >= 0; --i)
-                        s = s * 64 + (int64_t)__float2int_rn(__uint_as_float(r[NA_LIMB * ib + i]));
-                    const uint32_t v = barrett((uint64_t)(s + (int64_t)tp.off), tp.p, tp.mu);
-                    const int I = c0 / NA_LIMB + ib;
-                    sred[warp * TILE_OUT + I * TT + lane] = barrett((uint64_t)v * wj, tp.p, tp.mu);
+                        sum = sum * 64 + (int64_t)__float2int_rn(__uint_as_float(rr[NA_LIMB * ib + i]));
+                    const uint32_t v = barrett((uint64_t)(sum + (int64_t)tp.off), tp.p, tp.mu);
+                    uint32_t x = barrett((uint64_t)v * wj, tp.p, tp.mu);
+                    x += __shfl_xor_sync(0xffffffffu, x, 8);   // limbs j and j^1
+                    x = barrett((uint64_t)x, tp.p, tp.mu);
+                    x += __shfl_xor_sync(0xffffffffu, x, 16);  // and j^2
+                    const int g = (I0 + c0 / NA_LIMB + ib) * TT + r;
+                    if (j == 0 && g < L) c[g] = barrett((uint64_t)x, tp.p, tp.mu);
                 }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        for (int o = tid; o < TILE_OUT; o += TC_THREADS) {
-            const int g = I0 * TT + o;
-            if (g < L) {
-                const uint64_t s = (uint64_t)sred[o] + sred[TILE_OUT + o] + sred[2 * TILE_OUT + o] +
-                                   sred[3 * TILE_OUT + o];
-                c[g] = barrett(s, tp.p, tp.mu);
-            }
-        }
         __syncthreads();
     }
     __syncthreads();
