@@ -15,11 +15,16 @@
 // 3. inverse column pass: per column the inverse length-N1 transform, the
 //    scale N^-1, and the store of the n+m-1 output words.
 // Every pass reads and writes each word once (3 HBM round trips in all).
-// Inside a pass the transforms run in shared memory: forward transforms are
-// decimation in frequency (natural order in, digit-reversed out), inverse
-// ones decimation in time (digit-reversed in, natural out), with radix-4
-// butterflies and one radix-2 stage when log2 of the length is odd, so no
-// reordering pass is needed.  N <= 4096 runs in one CTA per product.
+// Forward transforms are decimation in frequency (natural order in,
+// digit-reversed out), inverse ones decimation in time (digit-reversed in,
+// natural out), with radix-4 butterflies and one radix-2 stage when log2 of
+// the length is odd, so no reordering pass is needed.  The column transforms
+// run level by level in shared memory, 8 or 16 adjacent columns per CTA; the
+// length-4096 row transforms run as three radix-16 stages in registers (16
+// elements per thread, two radix-4 levels per stage) with two shared-memory
+// exchanges, and the pointwise product sits between the last forward and the
+// first inverse stage without leaving registers.  N <= 4096 runs in one CTA
+// per product.
 //
 // Arithmetic: values stay in [0, p), p < 2^30.  Multiplication by a table
 // constant w uses Shoup's precomputed quotient wq = floor(w 2^32 / p)
@@ -42,7 +47,6 @@ namespace pm {
 constexpr int NTT_N2_LOG = 12;               // row length of the four-step layout
 constexpr int NTT_N2 = 1 << NTT_N2_LOG;
 constexpr int NTT_MAX_LOG = 24;              // N1 <= 4096 keeps a column block in shared memory
-constexpr int COLS = 8;                      // columns per CTA in the column passes
 constexpr int NTT_THREADS = 512;
 
 struct NttMod {
@@ -72,7 +76,9 @@ __device__ __forceinline__ uint32_t mul_mont(uint32_t x, uint32_t y, const NttMo
 }
 
 // Frequency index k of output position `pos` of a forward transform of
-// length 2^logm (stage radices 2 (odd logm only) then 4, 4, ...).
+// length 2^logm (stage radices 2 (odd logm only) then 4, 4, ...): the base-4
+// digits of the position, read in reverse (after the leading binary digit
+// when logm is odd, which becomes the lowest digit of k).
 __host__ __device__ __forceinline__ int freq_of_pos(int pos, int logm) {
     int k = 0, mult = 1, lg = logm, rem = pos;
     if (lg & 1) {
@@ -90,12 +96,35 @@ __host__ __device__ __forceinline__ int freq_of_pos(int pos, int logm) {
     return k;
 }
 
-// In-place transforms of `cnt` arrays (base + t*stride, length 2^logm) in
-// shared memory by the whole CTA.  tw[e] = w_M^e (forward) or w_M^-e
-// (inverse) for e in [0, M), with its Shoup quotient.
-template <bool FWD>
-__device__ void smem_ntt(uint32_t* base, int stride, int cnt, int logm, const uint2* __restrict__ tw,
-                         uint32_t p) {
+// The same map with a bit reversal: reversing the bits of a 2L-bit number
+// and then swapping the two bits of every pair reverses its base-4 digits.
+__device__ __forceinline__ uint32_t freq_of_pos_fast(uint32_t pos, int logm) {
+    uint32_t hi = 0, rest = pos;
+    int lg = logm;
+    if (lg & 1) {
+        --lg;
+        hi = rest >> lg;
+        rest &= (1u << lg) - 1;
+    }
+    if (lg == 0) return hi;
+    uint32_t r = __brev(rest) >> (32 - lg);
+    r = ((r & 0x55555555u) << 1) | ((r >> 1) & 0x55555555u);
+    return (logm & 1) ? hi + 2 * r : r;
+}
+
+// In-place transforms of `cnt` arrays of length M = 2^logm in shared memory
+// by the whole CTA: element e of array t is base[t * ts + e * es].  With
+// `fast_t`, consecutive threads take consecutive arrays (for arrays stored
+// side by side, es = cnt); otherwise consecutive elements of one array.
+// tw[e] = w_M^e (forward) or w_M^-e (inverse) for e in [0, M), with its Shoup
+// quotient.
+template <bool FWD, int CNT_FAST = 0>
+__device__ void smem_ntt(uint32_t* base, int es, int ts, int cnt, bool fast_t, int logm,
+                         const uint2* __restrict__ tw, uint32_t p) {
+    if (CNT_FAST) {  // arrays side by side, CNT_FAST of them (a power of two)
+        cnt = CNT_FAST;
+        fast_t = true;
+    }
     const int M = 1 << logm;
     const uint2 w4 = __ldg(tw + (M >> 2));  // primitive 4th root (or its inverse)
     const int quarter = M >> 2;
@@ -103,11 +132,12 @@ __device__ void smem_ntt(uint32_t* base, int stride, int cnt, int logm, const ui
     if (FWD && (logm & 1)) {  // radix-2 stage, span M/2
         const int h = M >> 1;
         for (int idx = threadIdx.x; idx < cnt * h; idx += blockDim.x) {
-            const int t = idx >> (logm - 1), j = idx & (h - 1);
-            uint32_t* x = base + t * stride;
-            const uint32_t u = x[j], v = x[j + h];
-            x[j] = add_p(u, v, p);
-            x[j + h] = mul_shoup(sub_p(u, v, p), __ldg(tw + j), p);
+            const int t = CNT_FAST ? (idx & (CNT_FAST - 1)) : fast_t ? idx % cnt : idx >> (logm - 1);
+            const int j = CNT_FAST ? (idx / CNT_FAST) : fast_t ? idx / cnt : idx & (h - 1);
+            uint32_t* x = base + t * ts;
+            const uint32_t u = x[j * es], v = x[(j + h) * es];
+            x[j * es] = add_p(u, v, p);
+            x[(j + h) * es] = mul_shoup(sub_p(u, v, p), __ldg(tw + j), p);
         }
         __syncthreads();
     }
@@ -116,11 +146,13 @@ __device__ void smem_ntt(uint32_t* base, int stride, int cnt, int logm, const ui
         const int lgs = FWD ? (logm & 1 ? logm - 3 : logm - 2) - 2 * it : 2 * it;  // log2 s
         const int lgstep = logm - 2 - lgs;  // twiddle exponent step M/(4s)
         for (int idx = threadIdx.x; idx < nbf4; idx += blockDim.x) {
-            const int t = idx >> (logm - 2), b = idx & (quarter - 1);
+            const int t = CNT_FAST ? (idx & (CNT_FAST - 1)) : fast_t ? idx % cnt : idx >> (logm - 2);
+            const int b = CNT_FAST ? (idx / CNT_FAST) : fast_t ? idx / cnt : idx & (quarter - 1);
             const int blk = b >> lgs, j = b & (s - 1);
-            uint32_t* x = base + t * stride + (blk << (lgs + 2)) + j;
+            uint32_t* x = base + t * ts + ((blk << (lgs + 2)) + j) * es;
             const int e = j << lgstep;
-            uint32_t x0 = x[0], x1 = x[s], x2 = x[2 * s], x3 = x[3 * s];
+            const int se = s * es;
+            uint32_t x0 = x[0], x1 = x[se], x2 = x[2 * se], x3 = x[3 * se];
             if (!FWD) {  // decimation in time: twiddle the inputs
                 x1 = mul_shoup(x1, __ldg(tw + e), p);
                 x2 = mul_shoup(x2, __ldg(tw + 2 * e), p);
@@ -135,21 +167,90 @@ __device__ void smem_ntt(uint32_t* base, int stride, int cnt, int logm, const ui
                 z2 = mul_shoup(z2, __ldg(tw + 2 * e), p);
                 z3 = mul_shoup(z3, __ldg(tw + 3 * e), p);
             }
-            x[0] = z0; x[s] = z1; x[2 * s] = z2; x[3 * s] = z3;
+            x[0] = z0; x[se] = z1; x[2 * se] = z2; x[3 * se] = z3;
         }
         __syncthreads();
     }
     if (!FWD && (logm & 1)) {  // radix-2 stage, span M/2
         const int h = M >> 1;
         for (int idx = threadIdx.x; idx < cnt * h; idx += blockDim.x) {
-            const int t = idx >> (logm - 1), j = idx & (h - 1);
-            uint32_t* x = base + t * stride;
-            const uint32_t u = x[j], v = mul_shoup(x[j + h], __ldg(tw + j), p);
-            x[j] = add_p(u, v, p);
-            x[j + h] = sub_p(u, v, p);
+            const int t = CNT_FAST ? (idx & (CNT_FAST - 1)) : fast_t ? idx % cnt : idx >> (logm - 1);
+            const int j = CNT_FAST ? (idx / CNT_FAST) : fast_t ? idx / cnt : idx & (h - 1);
+            uint32_t* x = base + t * ts;
+            const uint32_t u = x[j * es], v = mul_shoup(x[(j + h) * es], __ldg(tw + j), p);
+            x[j * es] = add_p(u, v, p);
+            x[(j + h) * es] = sub_p(u, v, p);
         }
         __syncthreads();
     }
+}
+
+// One radix-4 butterfly on registers with twiddle exponent e (the same
+// network as smem_ntt's; e = 0 needs no multiplications).
+template <bool FWD>
+__device__ __forceinline__ void bf4(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint2 w4,
+                                    const uint2* __restrict__ tw, int e, uint32_t p) {
+    if (!FWD && e) {
+        x1 = mul_shoup(x1, __ldg(tw + e), p);
+        x2 = mul_shoup(x2, __ldg(tw + 2 * e), p);
+        x3 = mul_shoup(x3, __ldg(tw + 3 * e), p);
+    }
+    const uint32_t t0 = add_p(x0, x2, p), t1 = sub_p(x0, x2, p);
+    const uint32_t t2 = add_p(x1, x3, p), t3 = mul_shoup(sub_p(x1, x3, p), w4, p);
+    x0 = add_p(t0, t2, p);
+    x2 = sub_p(t0, t2, p);
+    x1 = add_p(t1, t3, p);
+    x3 = sub_p(t1, t3, p);
+    if (FWD && e) {
+        x1 = mul_shoup(x1, __ldg(tw + e), p);
+        x2 = mul_shoup(x2, __ldg(tw + 2 * e), p);
+        x3 = mul_shoup(x3, __ldg(tw + 3 * e), p);
+    }
+}
+
+// A length-4096 transform as three radix-16 stages, each two radix-4 levels
+// done in registers by 256 threads holding 16 elements (the levels of
+// smem_ntt with logm = 12, grouped by the elements they touch):
+//   stage 1: elements t + 256 l      (levels s = 1024, 256)
+//   stage 2: elements B + t' + 16 l   (B = 256 (t / 16), t' = t mod 16; levels s = 64, 16)
+//   stage 3: elements 16 t + l        (levels s = 4, 1)
+// Forward runs stages 1, 2, 3 (levels large to small); the inverse 3, 2, 1
+// with the levels reversed.  Shared arrays use one pad word per 16 words.
+__device__ __forceinline__ int rphys(int i) { return i + (i >> 4); }
+constexpr int ROW_WORDS = NTT_N2 + NTT_N2 / 16;
+
+template <bool FWD>
+__device__ __forceinline__ void row_stage(int stage, uint32_t (&r)[16], uint2 w4, const uint2* __restrict__ tw,
+                                          uint32_t p) {
+    const int t = threadIdx.x, tp = t & 15;
+    if (FWD) {
+#pragma unroll
+        for (int l0 = 0; l0 < 4; ++l0) {
+            const int e = stage == 1 ? t + 256 * l0 : stage == 2 ? 16 * (tp + 16 * l0) : 256 * l0;
+            bf4<true>(r[l0], r[l0 + 4], r[l0 + 8], r[l0 + 12], w4, tw, e, p);
+        }
+#pragma unroll
+        for (int l1 = 0; l1 < 4; ++l1) {
+            const int e = stage == 1 ? 4 * t : stage == 2 ? 64 * tp : 0;
+            bf4<true>(r[4 * l1], r[4 * l1 + 1], r[4 * l1 + 2], r[4 * l1 + 3], w4, tw, e, p);
+        }
+    } else {
+#pragma unroll
+        for (int l1 = 0; l1 < 4; ++l1) {
+            const int e = stage == 1 ? 4 * t : stage == 2 ? 64 * tp : 0;
+            bf4<false>(r[4 * l1], r[4 * l1 + 1], r[4 * l1 + 2], r[4 * l1 + 3], w4, tw, e, p);
+        }
+#pragma unroll
+        for (int l0 = 0; l0 < 4; ++l0) {
+            const int e = stage == 1 ? t + 256 * l0 : stage == 2 ? 16 * (tp + 16 * l0) : 256 * l0;
+            bf4<false>(r[l0], r[l0 + 4], r[l0 + 8], r[l0 + 12], w4, tw, e, p);
+        }
+    }
+}
+
+// element index of register l of thread t in stage `stage`
+__device__ __forceinline__ int row_index(int stage, int t, int l) {
+    return stage == 1 ? t + 256 * l : stage == 2 ? 256 * (t >> 4) + (t & 15) + 16 * l : 16 * t + l;
 }
 
 // Device tables of one (p, g, log N), each entry (w, floor(w 2^32 / p)).
@@ -180,78 +281,146 @@ __global__ void __launch_bounds__(NTT_THREADS) ntt_small_kernel(
         sb[i] = i < m ? b[i] : 0u;
     }
     __syncthreads();
-    smem_ntt<true>(sh, N, 2, logn, tb.lo, md.p);
+    smem_ntt<true>(sh, 1, N, 2, false, logn, tb.lo, md.p);
     for (int i = threadIdx.x; i < N; i += blockDim.x) sa[i] = mul_mont(sa[i], sb[i], md);
     __syncthreads();
-    smem_ntt<false>(sa, N, 1, logn, tb.ilo, md.p);
+    smem_ntt<false>(sa, 1, N, 1, false, logn, tb.ilo, md.p);
     for (int i = threadIdx.x; i < L; i += blockDim.x) c[i] = mul_shoup(sa[i], tb.scale, md.p);
 }
 
+__device__ __forceinline__ void cp_async4_ntt(uint32_t* dst, const uint32_t* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
 // ---- four-step pass 1: forward column transforms of a (y = 0) and b (y = 1) ----
+// A CTA takes `cols` adjacent columns; shared memory holds them row by row
+// ([n1][cols]), so loads and stores touch 4*cols contiguous bytes per row and
+// the butterflies of the `cols` columns run side by side.
+template <int COLS>
 __global__ void __launch_bounds__(NTT_THREADS) ntt_col_fwd_kernel(
     const uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ b, int m,
     uint32_t* __restrict__ ta, uint32_t* __restrict__ tb_out, int logn1, NttTables tb, NttMod md) {
+    constexpr int cols = COLS;
     extern __shared__ uint32_t sh[];
-    const int N1 = 1 << logn1, stride = N1 + 1;
+    const int N1 = 1 << logn1;
     const uint32_t* x = blockIdx.y == 0 ? a : b;
     const int len = blockIdx.y == 0 ? n : m;
     uint32_t* out = blockIdx.y == 0 ? ta : tb_out;
-    const int c0 = blockIdx.x * COLS;
-    for (int idx = threadIdx.x; idx < COLS * N1; idx += blockDim.x) {
-        const int j = idx & (COLS - 1), n1 = idx / COLS;
+    const int c0 = blockIdx.x * cols;
+    for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
+        const int j = idx % cols, n1 = idx / cols;
         const int g = n1 * NTT_N2 + c0 + j;
-        sh[j * stride + n1] = g < len ? __ldg(x + g) : 0u;
+        cp_async4_ntt(sh + idx, x + (g < len ? g : 0), g < len);
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    smem_ntt<true>(sh, stride, COLS, logn1, tb.hi, md.p);
-    for (int idx = threadIdx.x; idx < COLS * N1; idx += blockDim.x) {
-        const int j = idx & (COLS - 1), pos = idx / COLS;
-        const uint32_t k1 = (uint32_t)freq_of_pos(pos, logn1);
-        const uint32_t e = (uint32_t)(((uint64_t)(c0 + j) * k1) & ((((uint64_t)N1) << NTT_N2_LOG) - 1));
-        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root(sh[j * stride + pos], e, tb.lo, tb.hi, md.p);
+    smem_ntt<true, COLS>(sh, cols, 1, cols, true, logn1, tb.hi, md.p);
+    const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
+    for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
+        const int j = idx % cols, pos = idx / cols;
+        const uint32_t k1 = freq_of_pos_fast((uint32_t)pos, logn1);
+        const uint32_t e = (uint32_t)(((uint64_t)(c0 + j) * k1) & nmask);
+        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root(sh[idx], e, tb.lo, tb.hi, md.p);
     }
 }
 
 // ---- four-step pass 2: per row, forward row transforms, product, inverse ----
-__global__ void __launch_bounds__(NTT_THREADS) ntt_row_kernel(uint32_t* __restrict__ ta,
-                                                              const uint32_t* __restrict__ tbuf,
-                                                              int logn1, NttTables tb, NttMod md) {
-    __shared__ uint32_t sh[2 * NTT_N2];
+__global__ void __launch_bounds__(256) ntt_row_kernel(uint32_t* __restrict__ ta,
+                                                      const uint32_t* __restrict__ tbuf,
+                                                      int logn1, NttTables tb, NttMod md) {
+    __shared__ uint32_t sA[ROW_WORDS];
+    __shared__ uint32_t sB[ROW_WORDS];
+    const int t = threadIdx.x;
     const size_t r0 = (size_t)blockIdx.x * NTT_N2;
-    for (int i = threadIdx.x; i < NTT_N2; i += blockDim.x) {
-        sh[i] = ta[r0 + i];
-        sh[NTT_N2 + i] = tbuf[r0 + i];
+    const uint32_t p = md.p;
+    const uint2 w4 = __ldg(tb.row + NTT_N2 / 4), iw4 = __ldg(tb.irow + NTT_N2 / 4);
+    uint32_t r[16], q[16];
+    // stage 1 of both rows, straight from global memory
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        r[l] = ta[r0 + t + 256 * l];
+        q[l] = tbuf[r0 + t + 256 * l];
+    }
+    row_stage<true>(1, r, w4, tb.row, p);
+    row_stage<true>(1, q, w4, tb.row, p);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        sA[rphys(t + 256 * l)] = r[l];
+        sB[rphys(t + 256 * l)] = q[l];
     }
     __syncthreads();
-    smem_ntt<true>(sh, NTT_N2, 2, NTT_N2_LOG, tb.row, md.p);
-    for (int i = threadIdx.x; i < NTT_N2; i += blockDim.x) sh[i] = mul_mont(sh[i], sh[NTT_N2 + i], md);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        r[l] = sA[rphys(row_index(2, t, l))];
+        q[l] = sB[rphys(row_index(2, t, l))];
+    }
+    row_stage<true>(2, r, w4, tb.row, p);
+    row_stage<true>(2, q, w4, tb.row, p);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        sA[rphys(row_index(2, t, l))] = r[l];
+        sB[rphys(row_index(2, t, l))] = q[l];
+    }
     __syncthreads();
-    smem_ntt<false>(sh, NTT_N2, 1, NTT_N2_LOG, tb.irow, md.p);
-    const uint32_t k1 = (uint32_t)freq_of_pos(blockIdx.x, logn1);
+    // stage 3, the pointwise product and the first inverse stage stay in registers
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        r[l] = sA[rphys(16 * t + l)];
+        q[l] = sB[rphys(16 * t + l)];
+    }
+    row_stage<true>(3, r, w4, tb.row, p);
+    row_stage<true>(3, q, w4, tb.row, p);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) r[l] = mul_mont(r[l], q[l], md);
+    row_stage<false>(3, r, iw4, tb.irow, p);
+    __syncthreads();  // every thread has read its stage-3 inputs from sA
+#pragma unroll
+    for (int l = 0; l < 16; ++l) sA[rphys(16 * t + l)] = r[l];
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < 16; ++l) r[l] = sA[rphys(row_index(2, t, l))];
+    row_stage<false>(2, r, iw4, tb.irow, p);
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < 16; ++l) sA[rphys(row_index(2, t, l))] = r[l];
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < 16; ++l) r[l] = sA[rphys(t + 256 * l)];
+    row_stage<false>(1, r, iw4, tb.irow, p);
+    const uint32_t k1 = freq_of_pos_fast(blockIdx.x, logn1);
     const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
-    for (int i = threadIdx.x; i < NTT_N2; i += blockDim.x) {
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        const int i = t + 256 * l;
         const uint32_t e = (uint32_t)(((uint64_t)i * k1) & nmask);
-        ta[r0 + i] = mul_root(sh[i], e, tb.ilo, tb.ihi, md.p);
+        ta[r0 + i] = mul_root(r[l], e, tb.ilo, tb.ihi, p);
     }
 }
 
 // ---- four-step pass 3: inverse column transforms, scale, store ----
+template <int COLS>
 __global__ void __launch_bounds__(NTT_THREADS) ntt_col_inv_kernel(const uint32_t* __restrict__ ta,
                                                                   uint32_t* __restrict__ c, int L,
                                                                   int logn1, NttTables tb, NttMod md) {
+    constexpr int cols = COLS;
     extern __shared__ uint32_t sh[];
-    const int N1 = 1 << logn1, stride = N1 + 1;
-    const int c0 = blockIdx.x * COLS;
-    for (int idx = threadIdx.x; idx < COLS * N1; idx += blockDim.x) {
-        const int j = idx & (COLS - 1), pos = idx / COLS;
-        sh[j * stride + pos] = ta[(size_t)pos * NTT_N2 + c0 + j];
+    const int N1 = 1 << logn1;
+    const int c0 = blockIdx.x * cols;
+    for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
+        const int j = idx % cols, pos = idx / cols;
+        cp_async4_ntt(sh + idx, ta + (size_t)pos * NTT_N2 + c0 + j, true);
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    smem_ntt<false>(sh, stride, COLS, logn1, tb.ihi, md.p);
-    for (int idx = threadIdx.x; idx < COLS * N1; idx += blockDim.x) {
-        const int j = idx & (COLS - 1), n1 = idx / COLS;
+    smem_ntt<false, COLS>(sh, cols, 1, cols, true, logn1, tb.ihi, md.p);
+    for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
+        const int j = idx % cols, n1 = idx / cols;
         const int64_t g = (int64_t)n1 * NTT_N2 + c0 + j;
-        if (g < L) c[g] = mul_shoup(sh[j * stride + n1], tb.scale, md.p);
+        if (g < L) c[g] = mul_shoup(sh[idx], tb.scale, md.p);
     }
 }
 
@@ -391,20 +560,30 @@ pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m,
     if (rc != PM_OK) return rc;
     uint32_t* ta = reinterpret_cast<uint32_t*>(sc->ntt);
     uint32_t* tbuf = ta + N;
-    const size_t col_smem = sizeof(uint32_t) * (size_t)COLS * (((size_t)1 << logn1) + 1);
+    const int cols = logn1 >= 12 ? 8 : 16;  // a CTA's columns: cols * N1 words of shared memory
+    const size_t col_smem = sizeof(uint32_t) * (size_t)cols * ((size_t)1 << logn1);
     static int col_done[64] = {};
     if (!col_done[ws->device]) {
-        const int mx = (int)(sizeof(uint32_t) * COLS * ((1 << (NTT_MAX_LOG - NTT_N2_LOG)) + 1));
-        e = cudaFuncSetAttribute(ntt_col_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (e != cudaSuccess) return cuda_fail(e);
-        e = cudaFuncSetAttribute(ntt_col_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-        if (e != cudaSuccess) return cuda_fail(e);
+        const int mx = (int)(sizeof(uint32_t) * 16 * (1 << (NTT_MAX_LOG - NTT_N2_LOG - 1)));
+        const void* ks[4] = {(const void*)ntt_col_fwd_kernel<8>, (const void*)ntt_col_fwd_kernel<16>,
+                             (const void*)ntt_col_inv_kernel<8>, (const void*)ntt_col_inv_kernel<16>};
+        for (const void* k : ks) {
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
         col_done[ws->device] = 1;
     }
-    ntt_col_fwd_kernel<<<dim3(NTT_N2 / COLS, 2), NTT_THREADS, col_smem, st>>>(a, (int)n, b, (int)m, ta,
-                                                                            tbuf, logn1, tb, md);
-    ntt_row_kernel<<<1u << logn1, NTT_THREADS, 0, st>>>(ta, tbuf, logn1, tb, md);
-    ntt_col_inv_kernel<<<NTT_N2 / COLS, NTT_THREADS, col_smem, st>>>(ta, c, (int)L, logn1, tb, md);
+    if (cols == 8)
+        ntt_col_fwd_kernel<8><<<dim3(NTT_N2 / 8, 2), NTT_THREADS, col_smem, st>>>(a, (int)n, b, (int)m, ta, tbuf,
+                                                                                logn1, tb, md);
+    else
+        ntt_col_fwd_kernel<16><<<dim3(NTT_N2 / 16, 2), NTT_THREADS, col_smem, st>>>(a, (int)n, b, (int)m, ta,
+                                                                                  tbuf, logn1, tb, md);
+    ntt_row_kernel<<<1u << logn1, 256, 0, st>>>(ta, tbuf, logn1, tb, md);
+    if (cols == 8)
+        ntt_col_inv_kernel<8><<<NTT_N2 / 8, NTT_THREADS, col_smem, st>>>(ta, c, (int)L, logn1, tb, md);
+    else
+        ntt_col_inv_kernel<16><<<NTT_N2 / 16, NTT_THREADS, col_smem, st>>>(ta, c, (int)L, logn1, tb, md);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     count_launches(3);
