@@ -161,84 +161,63 @@ __device__ __forceinline__ void load_group(const uint32_t* sA, int base, uint32_
     }
 }
 
-// Multiplication phase of one tile: acc[e] = sum over j in [jb0, jb1) of
-// a[d - j] b[j] for d = d0 + S*lane + e, a taken as zero outside [0, n).
-// Values stay congruent mod p and below 2^64 (see ModParams).
+// Multiplication phase of one staged chunk (CL coefficients of b and the
+// a-window they meet): acc[e] += sum over the chunk of a[d - j] b[j] for
+// d = d0 + S*lane + e.  Values stay congruent mod p and below 2^64 (see
+// ModParams); fold_ctr counts sub-steps since the last fold.
 template <int S>
-__device__ __forceinline__ void tile_accumulate(const uint32_t* __restrict__ a, int n,
-                                                const uint32_t* __restrict__ b, int d0, int jb0,
-                                                int jb1, const ModParams& mp, const Smem& sm,
-                                                uint64_t (&acc)[S]) {
+__device__ __forceinline__ void compute_chunk(const uint32_t* sA, const uint32_t* sB, int CL,
+                                              const ModParams& mp, uint64_t (&acc)[S], int& fold_ctr) {
     using C = Cfg<S>;
     constexpr int KB = C::KB, NGW = C::NGW, R = C::R;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    const int tot = CL / KB, qw = tot / WB, rw = tot % WB;
+    const int nsub = qw + (warp < rw ? 1 : 0);
+    const int r0 = KB * (warp * qw + min(warp, rw));
+    int base = S * lane + CL - KB - r0;  // window index of group 0 at the current sub-step
+    uint32_t ring[R][KB];
 #pragma unroll
-    for (int e = 0; e < S; ++e) acc[e] = 0;
-    int fold_ctr = 0;
-    const int nchunks = (jb1 - jb0 + CHUNK_MAX - 1) / CHUNK_MAX;
-    stage_chunk<S>(a, n, b, d0, chunk_dims<KB>(jb0, jb1, 0), sm.buf);
-    for (int ci = 0; ci < nchunks; ++ci) {
-        const ChunkDims ch = chunk_dims<KB>(jb0, jb1, ci);
-        if (ci + 1 < nchunks) {  // the next chunk streams in while this one is used
-            stage_chunk<S>(a, n, b, d0, chunk_dims<KB>(jb0, jb1, ci + 1),
-                           sm.buf + ((ci + 1) & 1) * C::BUF_WORDS);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        const uint32_t* sA = sm.buf + (ci & 1) * C::BUF_WORDS;
-        const uint32_t* sB = sA + C::A_WORDS;
-        const int CL = ch.CL;
-        const int tot = CL / KB, qw = tot / WB, rw = tot % WB;
-        const int nsub = qw + (warp < rw ? 1 : 0);
-        const int r0 = KB * (warp * qw + min(warp, rw));
-        int base = S * lane + CL - KB - r0;  // window index of group 0 at the current sub-step
-        uint32_t ring[R][KB];
+    for (int g = 0; g < NGW; ++g) load_group<S>(sA, base + g * KB, ring[(R - g) % R]);
+    const uint32_t* bp = sB + r0;
+    for (int q0 = 0; q0 < nsub; q0 += R) {
 #pragma unroll
-        for (int g = 0; g < NGW; ++g) load_group<S>(sA, base + g * KB, ring[(R - g) % R]);
-        const uint32_t* bp = sB + r0;
-        for (int q0 = 0; q0 < nsub; q0 += R) {
+        for (int u = 0; u < R; ++u) {
+            if (q0 + u < nsub) {
+                load_group<S>(sA, base - KB, ring[(u + 1) % R]);  // group 0 of the next sub-step
+                uint32_t bv[KB];
+                if constexpr (KB >= 4) {
 #pragma unroll
-            for (int u = 0; u < R; ++u) {
-                if (q0 + u < nsub) {
-                    load_group<S>(sA, base - KB, ring[(u + 1) % R]);  // group 0 of the next sub-step
-                    uint32_t bv[KB];
-                    if constexpr (KB >= 4) {
+                    for (int k4 = 0; k4 < KB; k4 += 4) {
+                        const uint4 v = *reinterpret_cast<const uint4*>(bp + k4);
+                        bv[k4] = v.x; bv[k4 + 1] = v.y; bv[k4 + 2] = v.z; bv[k4 + 3] = v.w;
+                    }
+                } else {
 #pragma unroll
-                        for (int k4 = 0; k4 < KB; k4 += 4) {
-                            const uint4 v = *reinterpret_cast<const uint4*>(bp + k4);
-                            bv[k4] = v.x; bv[k4 + 1] = v.y; bv[k4 + 2] = v.z; bv[k4 + 3] = v.w;
-                        }
+                    for (int k = 0; k < KB; ++k) bv[k] = bp[k];
+                }
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+#pragma unroll
+                    for (int e = 0; e < S; ++e) {
+                        const int t = e - k + KB - 1;  // window word of a[d - j]
+                        acc[e] = mad_wide(ring[(u - t / KB + R) % R][t % KB], bv[k], acc[e]);
+                    }
+                }
+                if (++fold_ctr == mp.fold_every) {
+                    fold_ctr = 0;
+                    if (mp.fold_twice) {
+#pragma unroll
+                        for (int e = 0; e < S; ++e) acc[e] = fold2(acc[e], mp.c32);
                     } else {
 #pragma unroll
-                        for (int k = 0; k < KB; ++k) bv[k] = bp[k];
+                        for (int e = 0; e < S; ++e) acc[e] = fold_once(acc[e], mp.c32);
                     }
-#pragma unroll
-                    for (int k = 0; k < KB; ++k) {
-#pragma unroll
-                        for (int e = 0; e < S; ++e) {
-                            const int t = e - k + KB - 1;  // window word of a[d - j]
-                            acc[e] = mad_wide(ring[(u - t / KB + R) % R][t % KB], bv[k], acc[e]);
-                        }
-                    }
-                    if (++fold_ctr == mp.fold_every) {
-                        fold_ctr = 0;
-                        if (mp.fold_twice) {
-#pragma unroll
-                            for (int e = 0; e < S; ++e) acc[e] = fold2(acc[e], mp.c32);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < S; ++e) acc[e] = fold_once(acc[e], mp.c32);
-                        }
-                    }
-                    base -= KB;
-                    bp += KB;
                 }
+                base -= KB;
+                bp += KB;
             }
         }
-        __syncthreads();  // this buffer is refilled two chunks later
     }
 }
 
@@ -308,8 +287,112 @@ struct Split {
     }
 };
 
+// One segment of a CTA's range: the part [x, x_end) of tile t of one pair.
+struct Seg {
+    const uint32_t* a;
+    const uint32_t* b;
+    uint32_t* c;
+    int n, m;              // n >= m (the longer operand slides through the window)
+    int d0;                // first output of the tile
+    int jb0, jb1;          // coefficients of b of this segment
+    int nchunks;
+    int64_t x, x_end, s_tile, e_tile;  // positions
+};
+
+// Walks a CTA's segments in order: pi = current pair, t = tile of the last
+// segment in it (-1: not known, search).
+template <int S, bool BATCH>
+__device__ __forceinline__ Seg make_seg(int64_t x, int64_t x1, int& pi, int64_t& t,
+                                        const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
+                                        const uint32_t* __restrict__ b_data, const int64_t* __restrict__ b_off,
+                                        uint32_t* __restrict__ c_data, const int64_t* __restrict__ c_off,
+                                        int n1, int m1, const int64_t* __restrict__ prefix) {
+    using C = Cfg<S>;
+    Seg sg;
+    int64_t pbase = 0;
+    if constexpr (BATCH) {
+        while (prefix[pi + 1] <= x) { ++pi; t = -1; }
+        pbase = prefix[pi];
+        sg.a = a_data + a_off[pi];
+        sg.b = b_data + b_off[pi];
+        sg.c = c_data + c_off[pi];
+        sg.n = (int)(a_off[pi + 1] - a_off[pi]);
+        sg.m = (int)(b_off[pi + 1] - b_off[pi]);
+    } else {
+        sg.a = a_data; sg.b = b_data; sg.c = c_data; sg.n = n1; sg.m = m1;
+    }
+    if (sg.n < sg.m) {
+        const uint32_t* tp = sg.a; sg.a = sg.b; sg.b = tp;
+        const int tn = sg.n; sg.n = sg.m; sg.m = tn;
+    }
+    const int64_t nt = ntiles_of(sg.n, sg.m, C::TD);
+    if (t >= 0) {
+        ++t;  // the previous segment ended with its tile: x starts the next one
+    } else {
+        const int64_t y = x - pbase;
+        int64_t tlo = 0, thi = nt;
+        while (thi - tlo > 1) {
+            const int64_t mid = (tlo + thi) >> 1;
+            if (cum_len(sg.n, sg.m, C::TD, mid) <= y) tlo = mid; else thi = mid;
+        }
+        t = tlo;
+    }
+    sg.s_tile = pbase + cum_len(sg.n, sg.m, C::TD, t);
+    sg.e_tile = pbase + cum_len(sg.n, sg.m, C::TD, t + 1);
+    sg.x = x;
+    sg.x_end = x1 < sg.e_tile ? x1 : sg.e_tile;
+    const int64_t jlo = tile_jlo(sg.n, C::TD, t);
+    sg.d0 = (int)(t * C::TD);
+    sg.jb0 = (int)(jlo + (x - sg.s_tile));
+    sg.jb1 = (int)(jlo + (sg.x_end - sg.s_tile));
+    sg.nchunks = (sg.jb1 - sg.jb0 + CHUNK_MAX - 1) / CHUNK_MAX;
+    if (t + 1 == nt) t = -1;  // the pair ends with this tile
+    return sg;
+}
+
+// Addition phase of a finished segment: the CTA's sums, then either the
+// tile's outputs (the CTA owns the whole tile) or a partial-sum slot; the CTA
+// that brings the tile's counter to its last value adds the slots and writes.
+template <int S>
+__device__ __forceinline__ void finish_segment(const Seg& sg, uint64_t (&acc)[S], const ModParams& mp,
+                                               const Smem& sm, const Split& sp, int64_t k, int64_t x0,
+                                               SkScratch sk, int* s_last) {
+    using C = Cfg<S>;
+    cta_reduce<S>(acc, mp, sm);
+    const int L = sg.n + sg.m - 1;
+    if (sg.x == sg.s_tile && sg.x_end == sg.e_tile) {
+        for (int o = threadIdx.x; o < C::TD; o += NT)
+            if (sg.d0 + o < L) sg.c[sg.d0 + o] = sm.red[o];
+        return;
+    }
+    const int64_t k1 = sp.owner(sg.s_tile), k2 = sp.owner(sg.e_tile - 1);
+    const int64_t slot = 2 * k + (sg.x == x0 ? 0 : 1);
+    uint32_t* mine = sk.slots + slot * C::TD;
+    for (int o = threadIdx.x; o < C::TD; o += NT) mine[o] = sm.red[o];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int seen = atomicAdd(&sk.counters[k1], 1u);
+        *s_last = (seen == (unsigned int)(k2 - k1)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*s_last) {  // every other contributor has written its slot
+        __threadfence();
+        const int64_t first_slot = 2 * k1 + (sp.start(k1) == sg.s_tile ? 0 : 1);
+        for (int o = threadIdx.x; o < C::TD; o += NT) {
+            uint64_t sum = __ldcg(sk.slots + first_slot * C::TD + o);
+            for (int64_t kk = k1 + 1; kk <= k2; ++kk) sum += __ldcg(sk.slots + 2 * kk * C::TD + o);
+            if (sg.d0 + o < L) sg.c[sg.d0 + o] = barrett(sum, mp.p, mp.mu);
+        }
+        if (threadIdx.x == 0) sk.counters[k1] = 0;
+    }
+    __syncthreads();  // s_last is read before the next segment may set it
+}
+
 // Persistent Stream-K kernel.  BATCH = false: one pair (a, n1, b, m1, c).
 // BATCH = true: pair i from the CSR arrays; prefix[i] = positions before pair i.
+// The CTA's chunks form one stream across its segments: the next chunk (of
+// this segment or the next) is copied in while the current one is used.
 template <int S, bool BATCH>
 __global__ void PM_BOUNDS plain_sk_kernel(
     const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
@@ -317,6 +400,7 @@ __global__ void PM_BOUNDS plain_sk_kernel(
     uint32_t* __restrict__ c_data, const int64_t* __restrict__ c_off, int n1, int m1,
     const int64_t* __restrict__ prefix, int batch, ModParams mp, SkScratch sk) {
     using C = Cfg<S>;
+    constexpr int KB = C::KB;
     extern __shared__ uint4 smem_raw[];
     __shared__ int s_last;
     const Smem sm = carve<S>(reinterpret_cast<uint32_t*>(smem_raw));
@@ -334,7 +418,6 @@ __global__ void PM_BOUNDS plain_sk_kernel(
     if (k >= P) return;
     const Split sp{G / P, G % P};
     const int64_t x0 = sp.start(k), x1 = sp.start(k + 1);
-    int64_t x = x0;
     // the pair holding x0 (binary search once; later segments move forward)
     int pi = 0;
     if constexpr (BATCH) {
@@ -345,78 +428,45 @@ __global__ void PM_BOUNDS plain_sk_kernel(
         }
         pi = lo;
     }
-    int64_t t = -1;  // tile of the previous segment within pair pi (-1: search)
-    while (x < x1) {
-        int64_t pbase = 0;
-        if constexpr (BATCH) {
-            while (prefix[pi + 1] <= x) { ++pi; t = -1; }
-            pbase = prefix[pi];
-        }
-        const uint32_t *a, *b;
-        uint32_t* c;
-        int n, m;
-        if constexpr (BATCH) {
-            a = a_data + a_off[pi];
-            b = b_data + b_off[pi];
-            c = c_data + c_off[pi];
-            n = (int)(a_off[pi + 1] - a_off[pi]);
-            m = (int)(b_off[pi + 1] - b_off[pi]);
-        } else {
-            a = a_data; b = b_data; c = c_data; n = n1; m = m1;
-        }
-        if (n < m) {  // the longer operand slides through the window
-            const uint32_t* tp = a; a = b; b = tp;
-            const int tn = n; n = m; m = tn;
-        }
-        const int64_t y = x - pbase;
-        if (t >= 0) {
-            ++t;  // segments follow each other: x is the start of the next tile
-        } else {
-            int64_t tlo = 0, thi = ntiles_of(n, m, C::TD);
-            while (thi - tlo > 1) {
-                const int64_t mid = (tlo + thi) >> 1;
-                if (cum_len(n, m, C::TD, mid) <= y) tlo = mid; else thi = mid;
-            }
-            t = tlo;
-        }
-        const int64_t s_tile = pbase + cum_len(n, m, C::TD, t);
-        const int64_t e_tile = pbase + cum_len(n, m, C::TD, t + 1);
-        const int64_t seg_end = x1 < e_tile ? x1 : e_tile;
-        const int64_t jlo = tile_jlo(n, C::TD, t);
-        const int d0 = (int)(t * C::TD);
-        uint64_t acc[S];
-        tile_accumulate<S>(a, n, b, d0, (int)(jlo + (x - s_tile)), (int)(jlo + (seg_end - s_tile)),
-                           mp, sm, acc);
-        cta_reduce<S>(acc, mp, sm);
-        const int L = n + m - 1;
-        if (x == s_tile && seg_end == e_tile) {  // the whole tile is ours
-            for (int o = threadIdx.x; o < C::TD; o += NT)
-                if (d0 + o < L) c[d0 + o] = sm.red[o];
-        } else {
-            const int64_t k1 = sp.owner(s_tile), k2 = sp.owner(e_tile - 1);
-            const int64_t slot = 2 * k + (x == x0 ? 0 : 1);
-            uint32_t* mine = sk.slots + slot * C::TD;
-            for (int o = threadIdx.x; o < C::TD; o += NT) mine[o] = sm.red[o];
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const unsigned int seen = atomicAdd(&sk.counters[k1], 1u);
-                s_last = (seen == (unsigned int)(k2 - k1)) ? 1 : 0;
-            }
-            __syncthreads();
-            if (s_last) {  // every other contributor has written its slot
-                __threadfence();
-                const int64_t first_slot = 2 * k1 + (sp.start(k1) == s_tile ? 0 : 1);
-                for (int o = threadIdx.x; o < C::TD; o += NT) {
-                    uint64_t sum = __ldcg(sk.slots + first_slot * C::TD + o);
-                    for (int64_t kk = k1 + 1; kk <= k2; ++kk) sum += __ldcg(sk.slots + 2 * kk * C::TD + o);
-                    if (d0 + o < L) c[d0 + o] = barrett(sum, mp.p, mp.mu);
-                }
-                if (threadIdx.x == 0) sk.counters[k1] = 0;
+    int64_t t = -1;
+    Seg cur = make_seg<S, BATCH>(x0, x1, pi, t, a_data, a_off, b_data, b_off, c_data, c_off, n1, m1, prefix);
+    int ci = 0, bi = 0, fold_ctr = 0;
+    uint64_t acc[S];
+    stage_chunk<S>(cur.a, cur.n, cur.b, cur.d0, chunk_dims<KB>(cur.jb0, cur.jb1, 0), sm.buf);
+    for (;;) {
+        Seg nxt = cur;
+        int nci = ci + 1;
+        bool has_next = true;
+        if (nci >= cur.nchunks) {
+            if (cur.x_end < x1) {
+                nxt = make_seg<S, BATCH>(cur.x_end, x1, pi, t, a_data, a_off, b_data, b_off, c_data, c_off,
+                                         n1, m1, prefix);
+                nci = 0;
+            } else {
+                has_next = false;
             }
         }
-        x = seg_end;
-        if (seg_end == e_tile && e_tile == pbase + cum_len(n, m, C::TD, ntiles_of(n, m, C::TD))) t = -1;
+        if (has_next) {  // the next chunk streams in while this one is used
+            stage_chunk<S>(nxt.a, nxt.n, nxt.b, nxt.d0, chunk_dims<KB>(nxt.jb0, nxt.jb1, nci),
+                           sm.buf + (bi ^ 1) * C::BUF_WORDS);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        if (ci == 0) {
+#pragma unroll
+            for (int e = 0; e < S; ++e) acc[e] = 0;
+            fold_ctr = 0;
+        }
+        const uint32_t* sA = sm.buf + bi * C::BUF_WORDS;
+        compute_chunk<S>(sA, sA + C::A_WORDS, chunk_dims<KB>(cur.jb0, cur.jb1, ci).CL, mp, acc, fold_ctr);
+        __syncthreads();  // this buffer is refilled by the next staging
+        if (ci == cur.nchunks - 1) finish_segment<S>(cur, acc, mp, sm, sp, k, x0, sk, &s_last);
+        if (!has_next) break;
+        cur = nxt;
+        ci = nci;
+        bi ^= 1;
     }
 }
 
