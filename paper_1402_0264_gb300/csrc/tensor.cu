@@ -60,7 +60,8 @@ constexpr int TC_MAXK = 4096;              // exactness bound on min(n, m)
 constexpr int TC_THREADS = 256;
 constexpr int GROUP_D = 8;                 // shifts per A-operand group (two groups in flight)
 constexpr int MAX_DELTA = TC_MAXK / TT + 2;            // shifts a tile can need
-constexpr int BD_LEN = TT * (MAX_DELTA + 2);           // b digits staged per limb
+constexpr int BD_SHIFT = 7;                            // staged b digit t sits at index t + 7
+constexpr int BD_LEN = TT * (MAX_DELTA + 2);           // b digits staged per limb (with the shift)
 constexpr int ROWS_MAX = NA_LIMB * (NBLK + MAX_DELTA + 2);
 constexpr int B_LBO = ROWS_MAX * 16;                   // bytes between K chunks of the a operand
 constexpr int H_Q = 4 * GROUP_D + 4;                  // Hankel core-matrix indices per group (4 G + 3 used)
@@ -72,7 +73,10 @@ constexpr int64_t WAIT_LIMIT = 1ll << 26;              // polls before a wait is
 constexpr int SM_B = 0;                                   // a operand: 4 chunks x ROWS_MAX rows
 constexpr int SM_H = SM_B + 4 * B_LBO;                    // 2 groups of Hankel core matrices
 constexpr int SM_BD = SM_H + 2 * H_SLOT;                  // b digits: NB_LIMB x BD_LEN bf16
-constexpr int SM_CTL = SM_BD + NB_LIMB * BD_LEN * 2;      // mbarriers, TMEM address, tile id
+constexpr int RAW_A = TT * (NBLK + MAX_DELTA);            // raw coefficients of a per tile
+constexpr int RAW_B = BD_LEN;                             // raw coefficients of b per tile
+constexpr int SM_RAW = SM_BD + NB_LIMB * BD_LEN * 2;      // the next tile's raw coefficients
+constexpr int SM_CTL = SM_RAW + 4 * (RAW_A + RAW_B);      // mbarriers, TMEM address, tile id
 constexpr int TC_SMEM = SM_CTL + 128;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -130,6 +134,69 @@ __device__ __forceinline__ int centred(uint32_t x, uint32_t p) {
     return x > (p - 1) / 2 ? (int)x - (int)p : (int)x;
 }
 
+// Geometry of one tile (see the kernel): pair, shifts, staged blocks.
+struct TcTile {
+    const uint32_t* a;
+    const uint32_t* b;
+    uint32_t* c;
+    int n, m, L, I0, d_lo, d_hi, nd, J_min, nJ, tb0;
+};
+
+__device__ __forceinline__ TcTile make_tile(int64_t tile, int batch, const uint32_t* __restrict__ a_data,
+                                            const int64_t* __restrict__ a_off, const uint32_t* __restrict__ b_data,
+                                            const int64_t* __restrict__ b_off, uint32_t* __restrict__ c_data,
+                                            const int64_t* __restrict__ c_off, const int64_t* __restrict__ prefix) {
+    TcTile tt;
+    int lo = 0, hi = batch;  // the pair: prefix[lo] <= tile < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= tile) lo = mid; else hi = mid;
+    }
+    tt.a = a_data + a_off[lo];
+    tt.b = b_data + b_off[lo];
+    tt.c = c_data + c_off[lo];
+    tt.n = (int)(a_off[lo + 1] - a_off[lo]);
+    tt.m = (int)(b_off[lo + 1] - b_off[lo]);
+    if (tt.m > tt.n) {  // b is the shorter operand (fewer shifts per tile)
+        const uint32_t* t = tt.a; tt.a = tt.b; tt.b = t;
+        const int tn = tt.n; tt.n = tt.m; tt.m = tn;
+    }
+    tt.L = tt.n + tt.m - 1;
+    tt.I0 = (int)(tile - prefix[lo]) * NBLK;           // first output block of the tile
+    const int NA = (tt.n + TT - 1) / TT;                // blocks of a
+    const int dmax = (tt.m + TT - 2) / TT;              // largest shift meeting b
+    tt.d_lo = max(0, tt.I0 - NA + 1);
+    tt.d_hi = min(dmax, tt.I0 + NBLK - 1);
+    tt.nd = tt.d_hi - tt.d_lo + 1;                      // >= 1 for a tile inside [0, L)
+    tt.J_min = tt.I0 - tt.d_hi;
+    tt.nJ = NBLK + tt.d_hi - tt.d_lo;                   // blocks J_min .. J_min + nJ - 1
+    tt.tb0 = TT * tt.d_lo - TT;                         // first staged b index
+    return tt;
+}
+
+// 4-byte asynchronous copy; with valid == false it writes a zero and reads nothing.
+__device__ __forceinline__ void cp_async4_tc(uint32_t* dst, const uint32_t* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+// Starts the copies of a tile's raw coefficients: a[32 J_min ..] (nJ blocks)
+// and b[tb0 ..] (32 (nd + 2) words), zeros outside the operands.
+__device__ __forceinline__ void prefetch_raw(const TcTile& tt, uint32_t* rawA, uint32_t* rawB) {
+    for (int q = threadIdx.x; q < tt.nJ * TT; q += blockDim.x) {
+        const int g = tt.J_min * TT + q;
+        const bool v = g >= 0 && g < tt.n;
+        cp_async4_tc(rawA + q, tt.a + (v ? g : 0), v);
+    }
+    for (int t = threadIdx.x; t < TT * (tt.nd + 2); t += blockDim.x) {
+        const int g = tt.tb0 + t;
+        const bool v = g >= 0 && g < tt.m;
+        cp_async4_tc(rawB + t, tt.b + (v ? g : 0), v);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 struct TcParams {
     uint32_t p;
     uint64_t mu;          // floor(2^64 / p)
@@ -146,6 +213,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     uint8_t* sB = sm + SM_B;
     uint8_t* sH = sm + SM_H;
     uint16_t* sbd = reinterpret_cast<uint16_t*>(sm + SM_BD);
+    uint32_t* rawA = reinterpret_cast<uint32_t*>(sm + SM_RAW);
+    uint32_t* rawB = rawA + RAW_A;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sm + SM_CTL);  // 2 mbarriers
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + SM_CTL + 32);
     int* s_tile = reinterpret_cast<int*>(sm + SM_CTL + 48);
@@ -171,53 +240,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     uint32_t parity[2] = {0, 0};
     const int64_t total = prefix[batch];
 
+    if (tid == 0) *s_tile = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    int64_t tile = *s_tile;
+    TcTile cur{};
+    if (tile < total) {
+        cur = make_tile(tile, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
+        prefetch_raw(cur, rawA, rawB);
+    }
     for (;;) {
-        if (tid == 0) *s_tile = (int)atomicAdd(counter, 1u);
-        __syncthreads();
-        const int64_t tile = *s_tile;
         if (tile >= total || *s_abort) break;
-        // pair of this tile
-        int lo = 0, hi = batch;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (prefix[mid] <= tile) lo = mid; else hi = mid;
-        }
-        const int pi = lo;
-        const uint32_t* a = a_data + a_off[pi];
-        const uint32_t* b = b_data + b_off[pi];
-        int n = (int)(a_off[pi + 1] - a_off[pi]);
-        int m = (int)(b_off[pi + 1] - b_off[pi]);
-        uint32_t* c = c_data + c_off[pi];
-        if (m > n) {  // b is the shorter operand (fewer shifts per tile)
-            const uint32_t* t = a; a = b; b = t;
-            const int tn = n; n = m; m = tn;
-        }
-        const int L = n + m - 1;
-        const int I0 = (int)(tile - prefix[pi]) * NBLK;        // first output block of the tile
-        const int NA = (n + TT - 1) / TT;                      // blocks of a
-        const int dmax = (m + TT - 2) / TT;                    // largest shift meeting b
-        const int d_lo = max(0, I0 - NA + 1);
-        const int d_hi = min(dmax, I0 + NBLK - 1);
-        const int nd = d_hi - d_lo + 1;                        // >= 1 for a tile inside [0, L)
-        const int J_min = I0 - d_hi;
-        const int nJ = NBLK + d_hi - d_lo;                     // blocks J_min .. J_min + nJ - 1
-        const int tb0 = TT * d_lo - TT;                        // first staged b index
+        uint32_t* c = cur.c;
+        const int L = cur.L, I0 = cur.I0;
+        const int d_lo = cur.d_lo, d_hi = cur.d_hi, nd = cur.nd, nJ = cur.nJ, tb0 = cur.tb0;
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        __syncthreads();
 
-        // ---- stage the b digits (natural order) and the a operand ----
+        // ---- digits of the staged coefficients: b (natural order) and the a operand ----
         for (int t = tid; t < TT * (nd + 2); t += TC_THREADS) {
-            const int g = tb0 + t;
-            int v = (g >= 0 && g < m) ? centred(__ldg(b + g), tp.p) : 0;
+            int v = centred(rawB[t], tp.p);
 #pragma unroll
             for (int j = 0; j < NB_LIMB; ++j) {
                 const int d = ((v + 128) & 255) - 128;
-                sbd[j * BD_LEN + t] = bf16_bits(d);
+                sbd[j * BD_LEN + BD_SHIFT + t] = bf16_bits(d);  // shifted: core matrices start 16-byte aligned
                 v = (v - d) >> 8;
             }
         }
         for (int q = tid; q < nJ * TT; q += TC_THREADS) {
             const int Jr = q / TT, k = q % TT;
-            const int g = (J_min + Jr) * TT + k;
-            int v = (g >= 0 && g < n) ? centred(__ldg(a + g), tp.p) : 0;
+            int v = centred(rawA[q], tp.p);
 #pragma unroll
             for (int i = 0; i < NA_LIMB; ++i) {
                 const int d = ((v + 32) & 63) - 32;
@@ -228,6 +279,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        // claim the next tile; its coefficients stream in while this tile's products run
+        if (tid == 0) *s_tile = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int64_t next = *s_tile;
+        TcTile nxt{};
+        if (next < total) {
+            nxt = make_tile(next, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
+            prefetch_raw(nxt, rawA, rawB);
+        }
 
         // ---- shifts in groups of GROUP_D: build the Toeplitz blocks, issue the MMAs ----
         const int ngroups = (nd + GROUP_D - 1) / GROUP_D;
@@ -245,17 +305,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             uint8_t* hslot = sH + buf * H_SLOT;
             const int nds = min(GROUP_D, nd - gi * GROUP_D);
             const int dg = d_lo + gi * GROUP_D;  // first shift of the group
-            // row t of H_j[q] (q = 4 dg + qq) holds d_j[-31 + 8 q + t .. + 7], 8 ascending digits
-            for (int w = tid; w < (4 * nds + 3) * NB_LIMB * 8; w += TC_THREADS) {
-                const int qq = w >> 5, j = (w >> 3) & 3, t = w & 7;
-                const int base = -31 + 8 * (4 * dg + qq) + t - tb0;  // staged index of the first digit
-                const uint16_t* src = sbd + j * BD_LEN + base;
-                uint4 v;
-                v.x = (uint32_t)src[0] | ((uint32_t)src[1] << 16);
-                v.y = (uint32_t)src[2] | ((uint32_t)src[3] << 16);
-                v.z = (uint32_t)src[4] | ((uint32_t)src[5] << 16);
-                v.w = (uint32_t)src[6] | ((uint32_t)src[7] << 16);
-                *reinterpret_cast<uint4*>(hslot + qq * 512 + j * 128 + t * 16) = v;
+            // core matrix H_j[q] (q = 4 dg + qq): row t holds d_j[-31 + 8 q + t .. + 7], 8 ascending
+            // digits; its 8 rows are the 16 digits from d_j[-31 + 8 q] shifted by 0..7
+            for (int w = tid; w < (4 * nds + 3) * NB_LIMB; w += TC_THREADS) {
+                const int qq = w >> 2, j = w & 3;
+                // staged index of d_j[-31 + 8 q] plus BD_SHIFT: a multiple of 8
+                const int i0 = BD_SHIFT - 31 + 8 * (4 * dg + qq) - tb0;
+                const uint4 lo4 = *reinterpret_cast<const uint4*>(sbd + j * BD_LEN + i0);
+                const uint4 hi4 = *reinterpret_cast<const uint4*>(sbd + j * BD_LEN + i0 + 8);
+                const uint32_t wd[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+                uint8_t* dst = hslot + qq * 512 + j * 128;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int k = t >> 1;
+                    uint4 v;
+                    if ((t & 1) == 0) {
+                        v = make_uint4(wd[k], wd[k + 1], wd[k + 2], wd[k + 3]);
+                    } else {
+                        v = make_uint4(__funnelshift_r(wd[k], wd[k + 1], 16), __funnelshift_r(wd[k + 1], wd[k + 2], 16),
+                                       __funnelshift_r(wd[k + 2], wd[k + 3], 16), __funnelshift_r(wd[k + 3], wd[k + 4], 16));
+                    }
+                    *reinterpret_cast<uint4*>(dst + t * 16) = v;
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
@@ -324,7 +395,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
+        cur = nxt;
+        tile = next;
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no copy outlives the CTA
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
