@@ -57,27 +57,45 @@ constexpr int NA_LIMB = 5, NB_LIMB = 4;
 constexpr int MMA_M = 128, MMA_N = NBLK * NA_LIMB;  // 240
 constexpr int TILE_OUT = TT * NBLK;        // 1536
 constexpr int TC_MAXK = 4096;              // exactness bound on min(n, m)
-constexpr int TC_THREADS = 256;
-constexpr int GROUP_D = 8;                 // shifts per A-operand group (two groups in flight)
+constexpr int GROUP_D = 8;                 // shifts per Hankel slot
+constexpr int NH = 4;                      // Hankel slots in the ring
 constexpr int MAX_DELTA = TC_MAXK / TT + 2;            // shifts a tile can need
 constexpr int BD_SHIFT = 7;                            // staged b digit t sits at index t + 7
 constexpr int BD_LEN = TT * (MAX_DELTA + 2);           // b digits staged per limb (with the shift)
+constexpr int BDS = BD_LEN + 16;                       // limb stride: 4 limbs on 4 distinct bank groups
 constexpr int ROWS_MAX = NA_LIMB * (NBLK + MAX_DELTA + 2);
 constexpr int B_LBO = ROWS_MAX * 16;                   // bytes between K chunks of the a operand
-constexpr int H_Q = 4 * GROUP_D + 4;                  // Hankel core-matrix indices per group (4 G + 3 used)
+constexpr int B_BUF = 4 * B_LBO;                       // one a operand (double-buffered across tiles)
+constexpr int H_Q = 4 * GROUP_D + 4;                   // Hankel core-matrix indices per slot (4 G + 3 used)
 constexpr int H_SLOT = H_Q * 512;                      // 4 limbs x 128-byte core matrices per index
-constexpr uint32_t TMEM_COLS = 256;
+constexpr uint32_t TMEM_COLS = 512;                    // two accumulators of 240 columns
+constexpr uint32_t ACC_STRIDE = 256;
 constexpr int64_t WAIT_LIMIT = 1ll << 26;              // polls before a wait is declared lost
+static_assert((BDS / 2) % 32 == 8, "limb stride must spread the limbs over the banks");
+
+// warp roles
+constexpr int PROD_WARP0 = 1, PROD_WARPS = 4, PROD_THREADS = 32 * PROD_WARPS;
+constexpr int EPI_WARP0 = PROD_WARP0 + PROD_WARPS, EPI_WARPS = 8;
+constexpr int TC_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);  // 416
 
 // shared memory map (bytes)
-constexpr int SM_B = 0;                                   // a operand: 4 chunks x ROWS_MAX rows
-constexpr int SM_H = SM_B + 4 * B_LBO;                    // 2 groups of Hankel core matrices
-constexpr int SM_BD = SM_H + 2 * H_SLOT;                  // b digits: NB_LIMB x BD_LEN bf16
-constexpr int RAW_A = TT * (NBLK + MAX_DELTA);            // raw coefficients of a per tile
-constexpr int RAW_B = BD_LEN;                             // raw coefficients of b per tile
-constexpr int SM_RAW = SM_BD + NB_LIMB * BD_LEN * 2;      // the next tile's raw coefficients
-constexpr int SM_CTL = SM_RAW + 4 * (RAW_A + RAW_B);      // mbarriers, TMEM address, tile id
-constexpr int TC_SMEM = SM_CTL + 128;
+constexpr int SM_B = 0;                                   // 2 a operands: 4 chunks x ROWS_MAX rows each
+constexpr int SM_H = SM_B + 2 * B_BUF;                    // ring of Hankel core-matrix slots
+constexpr int SM_BD = SM_H + NH * H_SLOT;                 // b digits: NB_LIMB x BDS bf16
+constexpr int SM_CTL = SM_BD + NB_LIMB * BDS * 2;         // mbarriers, tile records, TMEM address
+constexpr int CTL_TILES = 256, CTL_EPI = 448, CTL_MISC = 512;
+constexpr int TC_SMEM = SM_CTL + 576;
+
+// mbarriers (index into the control block)
+constexpr int BAR_STAGE_FULL = 0;   // [2] a operand + b digits of a tile staged (producer leader)
+constexpr int BAR_STAGE_EMPTY = 2;  // [2] MMAs of the tile that used the a operand done (commit)
+constexpr int BAR_H_FULL = 4;       // [NH] Hankel slot built (producer leader)
+constexpr int BAR_H_EMPTY = 8;      // [NH] MMAs reading the slot done (commit)
+constexpr int BAR_ACC_FULL = 12;    // [2] accumulator complete: record written + MMAs done (2 arrivals)
+constexpr int BAR_ACC_EMPTY = 14;   // [2] accumulator read back (one arrival per epilogue warp)
+constexpr int BAR_DRAIN = 16;       // all MMAs issued by the CTA done
+constexpr int NUM_BARS = 17;
+static_assert(NUM_BARS * 8 <= CTL_TILES, "control block");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -110,6 +128,15 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+// plain arrival (release at CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar) : "memory");
+}
+
 // Bounded wait for phase `parity` of an mbarrier; false if it ran out.
 __device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
     for (int64_t it = 0; it < WAIT_LIMIT; ++it) {
@@ -125,8 +152,20 @@ __device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-__device__ __forceinline__ uint16_t bf16_bits(int v) {
-    return __bfloat16_as_ushort(__float2bfloat16_rn((float)v));  // exact for |v| <= 256
+// barrier among the producer warps only
+__device__ __forceinline__ void producers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(PROD_THREADS) : "memory");
+}
+
+// bf16 bit pattern of a small integer (|d| <= 256 has at most 8 significant
+// bits, so the top half of its fp32 pattern is exact) in the top half of a word
+__device__ __forceinline__ uint32_t bf16_hi(int d) {
+    return __float_as_uint((float)d);
+}
+
+// two bf16 in one word: x in the low half, y in the high half
+__device__ __forceinline__ uint32_t pack2(uint32_t x, uint32_t y) {
+    return __byte_perm(x, y, 0x7632);
 }
 
 // balanced digits of the centred representative of x in [0, p)
@@ -139,8 +178,16 @@ struct TcTile {
     const uint32_t* a;
     const uint32_t* b;
     uint32_t* c;
-    int n, m, L, I0, d_lo, d_hi, nd, J_min, nJ, tb0;
+    int n, m, L, I0, d_lo, d_hi, nd, J_min, nJ, tb0, done;
 };
+static_assert(2 * sizeof(TcTile) <= CTL_EPI - CTL_TILES, "control block");
+
+// what the epilogue needs of a tile
+struct EpiInfo {
+    uint32_t* c;
+    int L, I0, done;
+};
+static_assert(2 * sizeof(EpiInfo) <= CTL_MISC - CTL_EPI, "control block");
 
 __device__ __forceinline__ TcTile make_tile(int64_t tile, int batch, const uint32_t* __restrict__ a_data,
                                             const int64_t* __restrict__ a_off, const uint32_t* __restrict__ b_data,
@@ -171,60 +218,135 @@ __device__ __forceinline__ TcTile make_tile(int64_t tile, int batch, const uint3
     tt.J_min = tt.I0 - tt.d_hi;
     tt.nJ = NBLK + tt.d_hi - tt.d_lo;                   // blocks J_min .. J_min + nJ - 1
     tt.tb0 = TT * tt.d_lo - TT;                         // first staged b index
+    tt.done = 0;
     return tt;
-}
-
-// 4-byte asynchronous copy; with valid == false it writes a zero and reads nothing.
-__device__ __forceinline__ void cp_async4_tc(uint32_t* dst, const uint32_t* src, bool valid) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
-                 : "memory");
-}
-
-// Starts the copies of a tile's raw coefficients: a[32 J_min ..] (nJ blocks)
-// and b[tb0 ..] (32 (nd + 2) words), zeros outside the operands.
-__device__ __forceinline__ void prefetch_raw(const TcTile& tt, uint32_t* rawA, uint32_t* rawB) {
-    for (int q = threadIdx.x; q < tt.nJ * TT; q += blockDim.x) {
-        const int g = tt.J_min * TT + q;
-        const bool v = g >= 0 && g < tt.n;
-        cp_async4_tc(rawA + q, tt.a + (v ? g : 0), v);
-    }
-    for (int t = threadIdx.x; t < TT * (tt.nd + 2); t += blockDim.x) {
-        const int g = tt.tb0 + t;
-        const bool v = g >= 0 && g < tt.m;
-        cp_async4_tc(rawB + t, tt.b + (v ? g : 0), v);
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
 struct TcParams {
     uint32_t p;
-    uint64_t mu;          // floor(2^64 / p)
-    uint64_t off;         // a multiple of p above 2^52 (makes signed limb sums non-negative)
-    uint32_t w256[NB_LIMB];  // 256^j mod p
+    uint64_t mu;             // floor(2^64 / p)
+    uint64_t off;            // a multiple of p above 2^52 (makes signed limb sums non-negative)
+    uint32_t wlo[NB_LIMB];   // 256^j mod p
+    uint32_t whi[NB_LIMB];   // 2^32 * 256^j mod p
 };
 
+// a operand of a tile: row (5 Jr + i) of K chunk kc holds limb i of
+// a[32 (J_min + Jr) + 31 - 8 kc - e] at element e (K runs backwards).  One
+// thread per block Jr: 32 coefficients, 5 limbs x 4 chunks of 16 bytes;
+// neighbouring threads write rows 80 bytes apart (distinct bank groups).
+__device__ __forceinline__ void stage_a(const TcTile& tt, uint8_t* sBb, int ptid, uint32_t p) {
+    const int base = TT * tt.J_min;
+    for (int Jr = ptid; Jr < tt.nJ; Jr += PROD_THREADS) {
+        int val[TT];
+#pragma unroll
+        for (int k = 0; k < TT; ++k) {
+            const int g = base + TT * Jr + k;
+            val[k] = (g >= 0 && g < tt.n) ? centred(__ldg(tt.a + g), p) : 0;
+        }
+        uint8_t* dst = sBb + NA_LIMB * Jr * 16;
+#pragma unroll
+        for (int i = 0; i < NA_LIMB; ++i) {
+            uint32_t f[TT];
+#pragma unroll
+            for (int k = 0; k < TT; ++k) {
+                const int d = ((val[k] + 32) & 63) - 32;
+                val[k] = (val[k] - d) >> 6;
+                f[k] = bf16_hi(d);
+            }
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {  // elements e = 0..7 are k = 31 - 8 kc - e
+                const int k0 = 31 - 8 * kc;
+                *reinterpret_cast<uint4*>(dst + kc * B_LBO + i * 16) =
+                    make_uint4(pack2(f[k0], f[k0 - 1]), pack2(f[k0 - 2], f[k0 - 3]), pack2(f[k0 - 4], f[k0 - 5]),
+                               pack2(f[k0 - 6], f[k0 - 7]));
+            }
+        }
+    }
+}
+
+// b digits in natural order: position x of limb j holds d_j[tb0 + x - BD_SHIFT].
+// One thread per 8 positions (positions 0..7 are never read).
+__device__ __forceinline__ void stage_b(const TcTile& tt, uint16_t* sbd, int ptid, uint32_t p) {
+    const int nu = 4 * tt.nd + 5;  // positions up to 32 nd + 39, the last one a Hankel row reads
+    for (int u = 1 + ptid; u < nu; u += PROD_THREADS) {
+        int val[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const int g = tt.tb0 + 8 * u + v - BD_SHIFT;
+            val[v] = (g >= 0 && g < tt.m) ? centred(__ldg(tt.b + g), p) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < NB_LIMB; ++j) {
+            uint32_t f[8];
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const int d = ((val[v] + 128) & 255) - 128;
+                val[v] = (val[v] - d) >> 8;
+                f[v] = bf16_hi(d);
+            }
+            *reinterpret_cast<uint4*>(sbd + j * BDS + 8 * u) =
+                make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+        }
+    }
+}
+
+// Hankel core matrices H_j[q], q = 4 dg + qq: row t holds d_j[-31 + 8 q + t .. + 7].
+// One thread per row; the 8 rows of one core matrix are 8 neighbouring
+// threads writing 128 contiguous bytes.
+__device__ __forceinline__ void build_hankel(const uint16_t* sbd, uint8_t* hslot, int nds, int dg, int tb0, int ptid) {
+    const uint32_t* sbw = reinterpret_cast<const uint32_t*>(sbd);
+    const int nrow = (4 * nds + 3) * NB_LIMB * 8;
+    const int ibase = BD_SHIFT - 31 + 32 * dg - tb0;  // staged index of d_j[-31 + 32 dg]: even
+    for (int rw = ptid; rw < nrow; rw += PROD_THREADS) {
+        const int t = rw & 7, j = (rw >> 3) & 3, qq = rw >> 5;
+        const int e0 = j * BDS + ibase + 8 * qq + t;
+        const uint32_t* wp = sbw + (e0 >> 1);
+        const uint32_t sh = (uint32_t)(t & 1) * 16;
+        const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2], w3 = wp[3], w4 = wp[4];
+        *reinterpret_cast<uint4*>(hslot + qq * 512 + j * 128 + t * 16) =
+            make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh), __funnelshift_r(w2, w3, sh),
+                       __funnelshift_r(w3, w4, sh));
+    }
+}
+
+// Warp-specialised persistent kernel.  Warp 0 issues the MMAs (one thread)
+// into two TMEM accumulators used by alternate tiles; warps 1-4 claim tiles,
+// stage the digits (a operand double-buffered) and build the Hankel slots
+// ahead of the MMAs; warps 5-12 read an accumulator back and reduce it while
+// the next tile accumulates into the other one.  The roles hand over through
+// mbarriers only.
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     int batch, const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
     const uint32_t* __restrict__ b_data, const int64_t* __restrict__ b_off,
     uint32_t* __restrict__ c_data, const int64_t* __restrict__ c_off, const int64_t* __restrict__ prefix,
     unsigned int* __restrict__ counter, TcParams tp, int* status) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    uint8_t* sB = sm + SM_B;
-    uint8_t* sH = sm + SM_H;
     uint16_t* sbd = reinterpret_cast<uint16_t*>(sm + SM_BD);
-    uint32_t* rawA = reinterpret_cast<uint32_t*>(sm + SM_RAW);
-    uint32_t* rawB = rawA + RAW_A;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + SM_CTL);  // 2 mbarriers
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + SM_CTL + 32);
-    int* s_tile = reinterpret_cast<int*>(sm + SM_CTL + 48);
-    int* s_abort = reinterpret_cast<int*>(sm + SM_CTL + 52);
+    TcTile* s_tiles = reinterpret_cast<TcTile*>(sm + SM_CTL + CTL_TILES);
+    EpiInfo* s_epi = reinterpret_cast<EpiInfo*>(sm + SM_CTL + CTL_EPI);
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + SM_CTL + CTL_MISC);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(sm + SM_CTL + CTL_MISC + 4);
+    volatile int* s_pstop = reinterpret_cast<volatile int*>(sm + SM_CTL + CTL_MISC + 8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t bar0 = smem_u32(bars), bar1 = smem_u32(bars + 1);
+    const uint32_t bar0 = smem_u32(sm + SM_CTL);
+    auto bar = [bar0](int i) { return bar0 + 8u * (uint32_t)i; };
+    auto fail = [status, s_abort]() {
+        atomicCAS(status, 0, (int)PM_ERR_TIMEOUT);
+        *s_abort = 1;
+    };
 
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1));
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar(BAR_STAGE_FULL + i), 1);
+            mbar_init(bar(BAR_STAGE_EMPTY + i), 1);
+            mbar_init(bar(BAR_ACC_FULL + i), 2);
+            mbar_init(bar(BAR_ACC_EMPTY + i), EPI_WARPS);
+        }
+        for (int i = 0; i < NH; ++i) {
+            mbar_init(bar(BAR_H_FULL + i), 1);
+            mbar_init(bar(BAR_H_EMPTY + i), 1);
+        }
+        mbar_init(bar(BAR_DRAIN), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *s_abort = 0;
     }
@@ -237,170 +359,202 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
-    uint32_t parity[2] = {0, 0};
     const int64_t total = prefix[batch];
 
-    if (tid == 0) *s_tile = (int)atomicAdd(counter, 1u);
-    __syncthreads();
-    int64_t tile = *s_tile;
-    TcTile cur{};
-    if (tile < total) {
-        cur = make_tile(tile, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
-        prefetch_raw(cur, rawA, rawB);
-    }
-    for (;;) {
-        if (tile >= total || *s_abort) break;
-        uint32_t* c = cur.c;
-        const int L = cur.L, I0 = cur.I0;
-        const int d_lo = cur.d_lo, d_hi = cur.d_hi, nd = cur.nd, nJ = cur.nJ, tb0 = cur.tb0;
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        __syncthreads();
-
-        // ---- digits of the staged coefficients: b (natural order) and the a operand ----
-        for (int t = tid; t < TT * (nd + 2); t += TC_THREADS) {
-            int v = centred(rawB[t], tp.p);
-#pragma unroll
-            for (int j = 0; j < NB_LIMB; ++j) {
-                const int d = ((v + 128) & 255) - 128;
-                sbd[j * BD_LEN + BD_SHIFT + t] = bf16_bits(d);  // shifted: core matrices start 16-byte aligned
-                v = (v - d) >> 8;
+    if (warp == 0) {
+        // ---------------- MMA issuer ----------------
+        uint32_t G = 0;  // Hankel groups consumed
+        for (int k = 0;; ++k) {
+            const int sb = k & 1;
+            int ok = 1;
+            if (lane == 0) {
+                ok = wait_parity(bar(BAR_STAGE_FULL + sb), (k >> 1) & 1);
+                if (ok && k >= 2) ok = wait_parity(bar(BAR_ACC_EMPTY + sb), ((k >> 1) - 1) & 1);
+                if (!ok) fail();
             }
-        }
-        for (int q = tid; q < nJ * TT; q += TC_THREADS) {
-            const int Jr = q / TT, k = q % TT;
-            int v = centred(rawA[q], tp.p);
-#pragma unroll
-            for (int i = 0; i < NA_LIMB; ++i) {
-                const int d = ((v + 32) & 63) - 32;
-                const int row = NA_LIMB * Jr + i, kr = TT - 1 - k;  // K runs backwards
-                *reinterpret_cast<uint16_t*>(sB + (kr >> 3) * B_LBO + row * 16 + (kr & 7) * 2) = bf16_bits(d);
-                v = (v - d) >> 6;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            const TcTile tt = s_tiles[sb];
+            if (lane == 0) {
+                s_epi[sb] = EpiInfo{tt.c, tt.L, tt.I0, tt.done};
+                mbar_arrive(bar(BAR_ACC_FULL + sb));  // the record (the second arrival is the MMAs')
+                if (tt.done) mbar_arrive(bar(BAR_ACC_FULL + sb));
             }
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        // claim the next tile; its coefficients stream in while this tile's products run
-        if (tid == 0) *s_tile = (int)atomicAdd(counter, 1u);
-        __syncthreads();
-        const int64_t next = *s_tile;
-        TcTile nxt{};
-        if (next < total) {
-            nxt = make_tile(next, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
-            prefetch_raw(nxt, rawA, rawB);
-        }
-
-        // ---- shifts in groups of GROUP_D: build the Toeplitz blocks, issue the MMAs ----
-        const int ngroups = (nd + GROUP_D - 1) / GROUP_D;
-        for (int gi = 0; gi < ngroups && !*s_abort; ++gi) {
-            const int buf = gi & 1;
-            if (gi >= 2) {
-                if (!wait_parity(buf ? bar1 : bar0, parity[buf])) {
-                    atomicCAS(status, 0, (int)PM_ERR_TIMEOUT);
-                    *s_abort = 1;
-                }
-                parity[buf] ^= 1u;
-            }
-            __syncthreads();
-            if (*s_abort) break;
-            uint8_t* hslot = sH + buf * H_SLOT;
-            const int nds = min(GROUP_D, nd - gi * GROUP_D);
-            const int dg = d_lo + gi * GROUP_D;  // first shift of the group
-            // core matrix H_j[q] (q = 4 dg + qq): row t holds d_j[-31 + 8 q + t .. + 7], 8 ascending
-            // digits; its 8 rows are the 16 digits from d_j[-31 + 8 q] shifted by 0..7
-            for (int w = tid; w < (4 * nds + 3) * NB_LIMB; w += TC_THREADS) {
-                const int qq = w >> 2, j = w & 3;
-                // staged index of d_j[-31 + 8 q] plus BD_SHIFT: a multiple of 8
-                const int i0 = BD_SHIFT - 31 + 8 * (4 * dg + qq) - tb0;
-                const uint4 lo4 = *reinterpret_cast<const uint4*>(sbd + j * BD_LEN + i0);
-                const uint4 hi4 = *reinterpret_cast<const uint4*>(sbd + j * BD_LEN + i0 + 8);
-                const uint32_t wd[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
-                uint8_t* dst = hslot + qq * 512 + j * 128;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int k = t >> 1;
-                    uint4 v;
-                    if ((t & 1) == 0) {
-                        v = make_uint4(wd[k], wd[k + 1], wd[k + 2], wd[k + 3]);
+            if (tt.done) break;
+            const uint32_t tacc = tmem + (uint32_t)sb * ACC_STRIDE;
+            const uint32_t sBa = smem_u32(sm + SM_B + sb * B_BUF);
+            const int ngroups = (tt.nd + GROUP_D - 1) / GROUP_D;
+            for (int gi = 0; gi < ngroups && ok; ++gi, ++G) {
+                const int slot = (int)(G % NH);
+                if (lane == 0) {
+                    ok = wait_parity(bar(BAR_H_FULL + slot), (G / NH) & 1);
+                    if (!ok) {
+                        fail();
                     } else {
-                        v = make_uint4(__funnelshift_r(wd[k], wd[k + 1], 16), __funnelshift_r(wd[k + 1], wd[k + 2], 16),
-                                       __funnelshift_r(wd[k + 2], wd[k + 3], 16), __funnelshift_r(wd[k + 3], wd[k + 4], 16));
-                    }
-                    *reinterpret_cast<uint4*>(dst + t * 16) = v;
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                for (int s = 0; s < nds; ++s) {
-                    const int d = dg + s;
-                    const uint32_t b_addr = smem_u32(sB) + (uint32_t)(NA_LIMB * (d_hi - d) * 16);
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t ha = smem_u32(sm + SM_H + slot * H_SLOT);
+                        const int nds = min(GROUP_D, tt.nd - gi * GROUP_D);
+                        const int dg = tt.d_lo + gi * GROUP_D;
+                        for (int s = 0; s < nds; ++s) {
+                            const uint32_t b_addr = sBa + (uint32_t)(NA_LIMB * (tt.d_hi - dg - s) * 16);
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint64_t da = smem_desc(smem_u32(hslot) + (uint32_t)((4 * s + 2 * h) * 512), 512, 128);
-                        const uint64_t db = smem_desc(b_addr + 2 * h * B_LBO, B_LBO, 128);
-                        mma_bf16(tmem, da, db, (gi == 0 && s == 0 && h == 0) ? 0u : 1u);
+                            for (int h = 0; h < 2; ++h) {
+                                const uint64_t da = smem_desc(ha + (uint32_t)((4 * s + 2 * h) * 512), 512, 128);
+                                const uint64_t db = smem_desc(b_addr + 2 * h * B_LBO, B_LBO, 128);
+                                mma_bf16(tacc, da, db, (gi == 0 && s == 0 && h == 0) ? 0u : 1u);
+                            }
+                        }
+                        mma_commit(bar(BAR_H_EMPTY + slot));
                     }
                 }
-                mma_commit(buf ? bar1 : bar0);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
             }
-        }
-        // ---- wait for the outstanding groups (in issue order) ----
-        for (int gi = max(0, ngroups - 2); gi < ngroups; ++gi) {
-            const int buf = gi & 1;
-            if (!*s_abort && !wait_parity(buf ? bar1 : bar0, parity[buf])) {
-                atomicCAS(status, 0, (int)PM_ERR_TIMEOUT);
-                *s_abort = 1;
+            if (!ok) break;
+            if (lane == 0) {
+                mma_commit(bar(BAR_STAGE_EMPTY + sb));
+                mma_commit(bar(BAR_ACC_FULL + sb));
             }
-            parity[buf] ^= 1u;
+            __syncwarp();
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (*s_abort) break;
-
-        // ---- epilogue: warp g reads TMEM lanes 32 g .. 32 g + 31 = (limb j, offset 8 g + t) ----
-        if (warp < 4) {
-            const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-            const int j = lane >> 3, r = 8 * warp + (lane & 7);
-            const uint64_t wj = tp.w256[j];
-            for (int c0 = 0; c0 < MMA_N; c0 += 80) {  // 16 blocks x 5 limbs per round
-                uint32_t rr[80];
+        if (lane == 0) {  // every MMA of this CTA completes before TMEM is released
+            mma_commit(bar(BAR_DRAIN));
+            if (!wait_parity(bar(BAR_DRAIN), 0)) fail();
+        }
+        __syncwarp();
+    } else if (warp < EPI_WARP0) {
+        // ---------------- producers ----------------
+        const int ptid = tid - 32 * PROD_WARP0;
+        uint32_t G = 0;  // Hankel groups built
+        for (int k = 0;; ++k) {
+            const int sb = k & 1;
+            if (ptid == 0) {
+                bool stop = *s_abort != 0;
+                const int64_t tile = stop ? total : (int64_t)atomicAdd(counter, 1u);
+                if (!stop && k >= 2 && !wait_parity(bar(BAR_STAGE_EMPTY + sb), ((k >> 1) - 1) & 1)) {
+                    fail();
+                    stop = true;
+                }
+                TcTile tt{};
+                if (!stop && tile < total)
+                    tt = make_tile(tile, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
+                else
+                    tt.done = 1;
+                s_tiles[sb] = tt;
+            }
+            producers_sync();
+            const TcTile tt = s_tiles[sb];
+            if (tt.done) {
+                if (ptid == 0) mbar_arrive(bar(BAR_STAGE_FULL + sb));
+                break;
+            }
+            stage_a(tt, sm + SM_B + sb * B_BUF, ptid, tp.p);
+            stage_b(tt, sbd, ptid, tp.p);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            producers_sync();
+            if (ptid == 0) mbar_arrive(bar(BAR_STAGE_FULL + sb));
+            const int ngroups = (tt.nd + GROUP_D - 1) / GROUP_D;
+            bool stop = false;
+            for (int gi = 0; gi < ngroups; ++gi, ++G) {
+                const int slot = (int)(G % NH);
+                if (ptid == 0) {
+                    bool st = *s_abort != 0;
+                    if (!st && G >= NH && !wait_parity(bar(BAR_H_EMPTY + slot), ((G / NH) - 1) & 1)) {
+                        fail();
+                        st = true;
+                    }
+                    *s_pstop = st;
+                }
+                producers_sync();
+                if (*s_pstop) {
+                    stop = true;
+                    break;
+                }
+                build_hankel(sbd, sm + SM_H + slot * H_SLOT, min(GROUP_D, tt.nd - gi * GROUP_D),
+                             tt.d_lo + gi * GROUP_D, tt.tb0, ptid);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                producers_sync();
+                if (ptid == 0) mbar_arrive(bar(BAR_H_FULL + slot));
+            }
+            if (stop) break;
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        // warp w reads TMEM lanes 32 (w % 4) .. + 31 = (limb j, offset 8 (w % 4) + t) and
+        // half of the columns (24 blocks); the 4 limbs of an output sit on lanes t, t + 8,
+        // t + 16, t + 24 and are combined by a reduce-scatter over 4 blocks at a time.
+        const int quarter = warp & 3, half = (warp - EPI_WARP0) >> 2;
+        const int j = lane >> 3, r = 8 * quarter + (lane & 7);
+        // (constant indices: a dynamic index would copy the parameters to local memory)
+        const uint32_t wlo = j == 0 ? tp.wlo[0] : j == 1 ? tp.wlo[1] : j == 2 ? tp.wlo[2] : tp.wlo[3];
+        const uint32_t whi = j == 0 ? tp.whi[0] : j == 1 ? tp.whi[1] : j == 2 ? tp.whi[2] : tp.whi[3];
+        for (int k = 0;; ++k) {
+            const int ab = k & 1;
+            int ok = 1;
+            if (lane == 0) {
+                ok = wait_parity(bar(BAR_ACC_FULL + ab), (k >> 1) & 1);
+                if (!ok) fail();
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+            const EpiInfo info = s_epi[ab];
+            if (info.done) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t tbase = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)ab * ACC_STRIDE +
+                                   (uint32_t)(half * (MMA_N / 2));
+#pragma unroll 1
+            for (int rd = 0; rd < 3; ++rd) {  // 8 blocks (40 columns) per round
+                uint32_t v[40];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
                     asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(rr[16 * q + 0]), "=r"(rr[16 * q + 1]), "=r"(rr[16 * q + 2]), "=r"(rr[16 * q + 3]),
-                          "=r"(rr[16 * q + 4]), "=r"(rr[16 * q + 5]), "=r"(rr[16 * q + 6]), "=r"(rr[16 * q + 7]),
-                          "=r"(rr[16 * q + 8]), "=r"(rr[16 * q + 9]), "=r"(rr[16 * q + 10]), "=r"(rr[16 * q + 11]),
-                          "=r"(rr[16 * q + 12]), "=r"(rr[16 * q + 13]), "=r"(rr[16 * q + 14]), "=r"(rr[16 * q + 15])
-                        : "r"(tmem + lane_base + (uint32_t)(c0 + 16 * q)));
+                        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                        : "=r"(v[8 * q + 0]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]),
+                          "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
+                        : "r"(tbase + (uint32_t)(40 * rd + 8 * q)));
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (rd == 2) {  // the accumulator is free once its last columns are in registers
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar(BAR_ACC_EMPTY + ab));
+                }
 #pragma unroll
-                for (int ib = 0; ib < 16; ++ib) {
-                    int64_t sum = 0;
+                for (int c4 = 0; c4 < 2; ++c4) {
+                    uint64_t x[4];
 #pragma unroll
-                    for (int i = NA_LIMB - 1; i >= 0; --i)
-                        sum = sum * 64 + (int64_t)__float2int_rn(__uint_as_float(rr[NA_LIMB * ib + i]));
-                    const uint32_t v = barrett((uint64_t)(sum + (int64_t)tp.off), tp.p, tp.mu);
-                    uint32_t x = barrett((uint64_t)v * wj, tp.p, tp.mu);
-                    x += __shfl_xor_sync(0xffffffffu, x, 8);   // limbs j and j^1
-                    x = barrett((uint64_t)x, tp.p, tp.mu);
-                    x += __shfl_xor_sync(0xffffffffu, x, 16);  // and j^2
-                    const int g = (I0 + c0 / NA_LIMB + ib) * TT + r;
-                    if (j == 0 && g < L) c[g] = barrett((uint64_t)x, tp.p, tp.mu);
+                    for (int be = 0; be < 4; ++be) {
+                        const uint32_t* dv = v + NA_LIMB * (4 * c4 + be);
+                        const int d0 = __float2int_rn(__uint_as_float(dv[0]));
+                        const int d1 = __float2int_rn(__uint_as_float(dv[1]));
+                        const int d2 = __float2int_rn(__uint_as_float(dv[2]));
+                        const int d3 = __float2int_rn(__uint_as_float(dv[3]));
+                        const int d4 = __float2int_rn(__uint_as_float(dv[4]));
+                        // sum_i 64^i d_i: d0 + 64 d1 and d2 + 64 d3 fit in 31 bits (|d_i| <= 2^24)
+                        int64_t sum = (int64_t)(d2 + 64 * d3) * 4096 + (int64_t)tp.off;
+                        sum += (int64_t)d4 * (1 << 24);
+                        sum += (int64_t)(d0 + 64 * d1);
+                        const uint64_t u = (uint64_t)sum;  // in [0, 2^53)
+                        x[be] = (uint64_t)(uint32_t)u * wlo + (uint64_t)(uint32_t)(u >> 32) * whi;  // < 2^61.01
+                    }
+                    // reduce-scatter over the limbs: lane (j, t) ends with block 4 c4 + j
+                    const bool o1 = (j & 1) != 0;
+                    const uint64_t keep0 = o1 ? x[1] : x[0], send0 = o1 ? x[0] : x[1];
+                    const uint64_t keep1 = o1 ? x[3] : x[2], send1 = o1 ? x[2] : x[3];
+                    const uint64_t y0 = keep0 + __shfl_xor_sync(0xffffffffu, send0, 8);
+                    const uint64_t y1 = keep1 + __shfl_xor_sync(0xffffffffu, send1, 8);
+                    const bool o2 = (j & 2) != 0;
+                    const uint64_t z = (o2 ? y1 : y0) + __shfl_xor_sync(0xffffffffu, o2 ? y0 : y1, 16);  // < 2^64
+                    const int blk = NBLK / 2 * half + 8 * rd + 4 * c4 + j;
+                    const int g = (info.I0 + blk) * TT + r;
+                    if (g < info.L) info.c[g] = barrett(z, tp.p, tp.mu);
                 }
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        cur = nxt;
-        tile = next;
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no copy outlives the CTA
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
 }
 
 // Planner: validates the CSR layout (degrees <= max_deg <= 4095) and builds
@@ -480,7 +634,8 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
     tp.off = ((1ull << 52) / p + 1) * (uint64_t)p;
     uint64_t w = 1;
     for (int j = 0; j < NB_LIMB; ++j) {
-        tp.w256[j] = (uint32_t)w;
+        tp.wlo[j] = (uint32_t)w;
+        tp.whi[j] = (uint32_t)((w << 32) % p);
         w = (w * 256) % p;
     }
     tc_plan_kernel<<<1, 1024, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg, prefix, counter, ws->status);
