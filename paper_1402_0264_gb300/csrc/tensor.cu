@@ -19,7 +19,8 @@
 // the K index runs backwards, k' = 31 - k, in both operands):
 //     D[(j, r)][(I, i)] = sum_delta sum_{k'<32} d_j[32 delta - 31 + r + k'] * e_i[32 (I - delta) + 31 - k']
 //                       = (e_i * d_j)[32 I + r].
-// For one shift delta this is one 128 x 240 x 32 product (two MMAs of K = 16):
+// For one shift delta this is one 128 x 240 x 32 product (two MMAs of K = 16),
+// narrowed after the tile's first shift to the columns whose a block exists:
 // N = 240 columns are 48 output blocks times the 5 limbs of a; the a operand
 // is stored once per tile as rows (J, i) = limb i of block J of a, reversed,
 // and the rows shift delta needs are the same rows moved by 5 per delta, so
@@ -73,10 +74,12 @@ constexpr uint32_t ACC_STRIDE = 256;
 constexpr int64_t WAIT_LIMIT = 1ll << 26;              // polls before a wait is declared lost
 static_assert((BDS / 2) % 32 == 8, "limb stride must spread the limbs over the banks");
 
-// warp roles
-constexpr int PROD_WARP0 = 1, PROD_WARPS = 4, PROD_THREADS = 32 * PROD_WARPS;
-constexpr int EPI_WARP0 = PROD_WARP0 + PROD_WARPS, EPI_WARPS = 8;
-constexpr int TC_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);  // 416
+// warp roles: 0 MMA issuer, 1-2 stagers (a operand), 3-6 builders (b digits,
+// Hankel slots), 7-14 epilogue
+constexpr int STG_WARP0 = 1, STG_WARPS = 2, STG_THREADS = 32 * STG_WARPS;
+constexpr int BLD_WARP0 = STG_WARP0 + STG_WARPS, BLD_WARPS = 4, BLD_THREADS = 32 * BLD_WARPS;
+constexpr int EPI_WARP0 = BLD_WARP0 + BLD_WARPS, EPI_WARPS = 8;
+constexpr int TC_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);  // 480
 
 // shared memory map (bytes)
 constexpr int SM_B = 0;                                   // 2 a operands: 4 chunks x ROWS_MAX rows each
@@ -87,9 +90,9 @@ constexpr int CTL_TILES = 256, CTL_EPI = 448, CTL_MISC = 512;
 constexpr int TC_SMEM = SM_CTL + 576;
 
 // mbarriers (index into the control block)
-constexpr int BAR_STAGE_FULL = 0;   // [2] a operand + b digits of a tile staged (producer leader)
+constexpr int BAR_A_FULL = 0;       // [2] tile record + a operand staged (stager leader)
 constexpr int BAR_STAGE_EMPTY = 2;  // [2] MMAs of the tile that used the a operand done (commit)
-constexpr int BAR_H_FULL = 4;       // [NH] Hankel slot built (producer leader)
+constexpr int BAR_H_FULL = 4;       // [NH] Hankel slot built (builder leader)
 constexpr int BAR_H_EMPTY = 8;      // [NH] MMAs reading the slot done (commit)
 constexpr int BAR_ACC_FULL = 12;    // [2] accumulator complete: record written + MMAs done (2 arrivals)
 constexpr int BAR_ACC_EMPTY = 14;   // [2] accumulator read back (one arrival per epilogue warp)
@@ -112,15 +115,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
-// instruction descriptor: D f32, A and B bf16, both K-major, N and M as given
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
-                           ((uint32_t)(MMA_M >> 4) << 24);
+// instruction descriptor: D f32, A and B bf16, both K-major, M = 128, N columns
+// (a multiple of 16, at most 256)
+__device__ __forceinline__ uint32_t idesc_n(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((uint32_t)(MMA_M >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t acc) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(IDESC), "r"(acc));
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -152,15 +157,32 @@ __device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-// barrier among the producer warps only
-__device__ __forceinline__ void producers_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(PROD_THREADS) : "memory");
+// Bounded wait by lane 0; once the phase has completed every lane waits on it
+// too (returning at once), so that each reader acquires what was released
+// before the arrival.  The result is the same on all lanes.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int lane) {
+    int ok = 1;
+    if (lane == 0) ok = wait_parity(bar, parity);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) wait_parity(bar, parity);
+    return ok != 0;
 }
 
-// bf16 bit pattern of a small integer (|d| <= 256 has at most 8 significant
-// bits, so the top half of its fp32 pattern is exact) in the top half of a word
-__device__ __forceinline__ uint32_t bf16_hi(int d) {
-    return __float_as_uint((float)d);
+// barriers among the stager warps and among the builder warps
+__device__ __forceinline__ void stagers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(STG_THREADS) : "memory");
+}
+__device__ __forceinline__ void builders_sync() {
+    asm volatile("bar.sync 2, %0;" ::"n"(BLD_THREADS) : "memory");
+}
+
+// Digit f - bias as an fp32 whose top half is its bf16 pattern (|f - bias| <= 128
+// has at most 8 significant bits).  The word 0x4B400000 is 1.5 * 2^23, whose
+// ulp is 1, so adding the integer f - bias to that word adds it to the value,
+// and subtracting 1.5 * 2^23 leaves it exactly.
+template <int BIAS>
+__device__ __forceinline__ uint32_t digit_bits(uint32_t f) {
+    return __float_as_uint(__uint_as_float(0x4B400000u - BIAS + f) - 12582912.0f);
 }
 
 // two bf16 in one word: x in the low half, y in the high half
@@ -178,7 +200,7 @@ struct TcTile {
     const uint32_t* a;
     const uint32_t* b;
     uint32_t* c;
-    int n, m, L, I0, d_lo, d_hi, nd, J_min, nJ, tb0, done;
+    int n, m, L, I0, na, d_lo, d_hi, nd, J_min, nJ, tb0, done;
 };
 static_assert(2 * sizeof(TcTile) <= CTL_EPI - CTL_TILES, "control block");
 
@@ -210,9 +232,9 @@ __device__ __forceinline__ TcTile make_tile(int64_t tile, int batch, const uint3
     }
     tt.L = tt.n + tt.m - 1;
     tt.I0 = (int)(tile - prefix[lo]) * NBLK;           // first output block of the tile
-    const int NA = (tt.n + TT - 1) / TT;                // blocks of a
+    tt.na = (tt.n + TT - 1) / TT;                       // blocks of a
     const int dmax = (tt.m + TT - 2) / TT;              // largest shift meeting b
-    tt.d_lo = max(0, tt.I0 - NA + 1);
+    tt.d_lo = max(0, tt.I0 - tt.na + 1);
     tt.d_hi = min(dmax, tt.I0 + NBLK - 1);
     tt.nd = tt.d_hi - tt.d_lo + 1;                      // >= 1 for a tile inside [0, L)
     tt.J_min = tt.I0 - tt.d_hi;
@@ -230,29 +252,32 @@ struct TcParams {
     uint32_t whi[NB_LIMB];   // 2^32 * 256^j mod p
 };
 
+// Balanced digits by an offset: with K = 32 (1 + 64 + ... + 64^4), u = v + K
+// lies in [0, 2^30) for |v| < p/2 < 2^28, its standard base-64 digits f_i give
+// v = sum (f_i - 32) 64^i, the balanced digits in [-32, 31].  Likewise base 256
+// with K = 128 (1 + 256 + 256^2 + 256^3) = 0x80808080 for the 4 digits of b.
+constexpr uint32_t K_A = 32u * (1u + 64u + 4096u + 262144u + 16777216u);
+constexpr uint32_t K_B = 0x80808080u;
+
 // a operand of a tile: row (5 Jr + i) of K chunk kc holds limb i of
 // a[32 (J_min + Jr) + 31 - 8 kc - e] at element e (K runs backwards).  One
 // thread per block Jr: 32 coefficients, 5 limbs x 4 chunks of 16 bytes;
 // neighbouring threads write rows 80 bytes apart (distinct bank groups).
-__device__ __forceinline__ void stage_a(const TcTile& tt, uint8_t* sBb, int ptid, uint32_t p) {
+__device__ __forceinline__ void stage_a(const TcTile& tt, uint8_t* sBb, int stid, uint32_t p) {
     const int base = TT * tt.J_min;
-    for (int Jr = ptid; Jr < tt.nJ; Jr += PROD_THREADS) {
-        int val[TT];
+    for (int Jr = stid; Jr < tt.nJ; Jr += STG_THREADS) {
+        uint32_t u[TT];
 #pragma unroll
         for (int k = 0; k < TT; ++k) {
             const int g = base + TT * Jr + k;
-            val[k] = (g >= 0 && g < tt.n) ? centred(__ldg(tt.a + g), p) : 0;
+            u[k] = (g >= 0 && g < tt.n) ? (uint32_t)centred(__ldg(tt.a + g), p) + K_A : K_A;
         }
         uint8_t* dst = sBb + NA_LIMB * Jr * 16;
 #pragma unroll
         for (int i = 0; i < NA_LIMB; ++i) {
             uint32_t f[TT];
 #pragma unroll
-            for (int k = 0; k < TT; ++k) {
-                const int d = ((val[k] + 32) & 63) - 32;
-                val[k] = (val[k] - d) >> 6;
-                f[k] = bf16_hi(d);
-            }
+            for (int k = 0; k < TT; ++k) f[k] = digit_bits<32>((u[k] >> (6 * i)) & 63u);
 #pragma unroll
             for (int kc = 0; kc < 4; ++kc) {  // elements e = 0..7 are k = 31 - 8 kc - e
                 const int k0 = 31 - 8 * kc;
@@ -265,39 +290,43 @@ __device__ __forceinline__ void stage_a(const TcTile& tt, uint8_t* sBb, int ptid
 }
 
 // b digits in natural order: position x of limb j holds d_j[tb0 + x - BD_SHIFT].
-// One thread per 8 positions (positions 0..7 are never read).
-__device__ __forceinline__ void stage_b(const TcTile& tt, uint16_t* sbd, int ptid, uint32_t p) {
+// One thread per 8 positions (positions 0..7 are never read), two groups of 8
+// per pass so that their loads are in flight together.
+__device__ __forceinline__ void stage_b_8(const uint32_t (&u)[8], uint16_t* dst) {
+#pragma unroll
+    for (int j = 0; j < NB_LIMB; ++j) {
+        uint32_t f[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) f[v] = digit_bits<128>(__byte_perm(u[v], 0, 0x4440 + j));
+        *reinterpret_cast<uint4*>(dst + j * BDS) =
+            make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+    }
+}
+
+__device__ __forceinline__ void stage_b(const TcTile& tt, uint16_t* sbd, int btid, uint32_t p) {
     const int nu = 4 * tt.nd + 5;  // positions up to 32 nd + 39, the last one a Hankel row reads
-    for (int u = 1 + ptid; u < nu; u += PROD_THREADS) {
-        int val[8];
+    for (int u0 = 1 + btid; u0 < nu; u0 += 2 * BLD_THREADS) {
+        const int u1 = u0 + BLD_THREADS;
+        uint32_t x0[8], x1[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
-            const int g = tt.tb0 + 8 * u + v - BD_SHIFT;
-            val[v] = (g >= 0 && g < tt.m) ? centred(__ldg(tt.b + g), p) : 0;
+            const int g0 = tt.tb0 + 8 * u0 + v - BD_SHIFT, g1 = g0 + 8 * BLD_THREADS;
+            x0[v] = (g0 >= 0 && g0 < tt.m) ? (uint32_t)centred(__ldg(tt.b + g0), p) + K_B : K_B;
+            x1[v] = (u1 < nu && g1 >= 0 && g1 < tt.m) ? (uint32_t)centred(__ldg(tt.b + g1), p) + K_B : K_B;
         }
-#pragma unroll
-        for (int j = 0; j < NB_LIMB; ++j) {
-            uint32_t f[8];
-#pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                const int d = ((val[v] + 128) & 255) - 128;
-                val[v] = (val[v] - d) >> 8;
-                f[v] = bf16_hi(d);
-            }
-            *reinterpret_cast<uint4*>(sbd + j * BDS + 8 * u) =
-                make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-        }
+        stage_b_8(x0, sbd + 8 * u0);
+        if (u1 < nu) stage_b_8(x1, sbd + 8 * u1);
     }
 }
 
 // Hankel core matrices H_j[q], q = 4 dg + qq: row t holds d_j[-31 + 8 q + t .. + 7].
 // One thread per row; the 8 rows of one core matrix are 8 neighbouring
 // threads writing 128 contiguous bytes.
-__device__ __forceinline__ void build_hankel(const uint16_t* sbd, uint8_t* hslot, int nds, int dg, int tb0, int ptid) {
+__device__ __forceinline__ void build_hankel(const uint16_t* sbd, uint8_t* hslot, int nds, int dg, int tb0, int btid) {
     const uint32_t* sbw = reinterpret_cast<const uint32_t*>(sbd);
     const int nrow = (4 * nds + 3) * NB_LIMB * 8;
     const int ibase = BD_SHIFT - 31 + 32 * dg - tb0;  // staged index of d_j[-31 + 32 dg]: even
-    for (int rw = ptid; rw < nrow; rw += PROD_THREADS) {
+    for (int rw = btid; rw < nrow; rw += BLD_THREADS) {
         const int t = rw & 7, j = (rw >> 3) & 3, qq = rw >> 5;
         const int e0 = j * BDS + ibase + 8 * qq + t;
         const uint32_t* wp = sbw + (e0 >> 1);
@@ -310,11 +339,12 @@ __device__ __forceinline__ void build_hankel(const uint16_t* sbd, uint8_t* hslot
 }
 
 // Warp-specialised persistent kernel.  Warp 0 issues the MMAs (one thread)
-// into two TMEM accumulators used by alternate tiles; warps 1-4 claim tiles,
-// stage the digits (a operand double-buffered) and build the Hankel slots
-// ahead of the MMAs; warps 5-12 read an accumulator back and reduce it while
-// the next tile accumulates into the other one.  The roles hand over through
-// mbarriers only.
+// into two TMEM accumulators used by alternate tiles; warps 1-2 claim tiles and
+// stage the a operand (double-buffered, so the next tile's is ready before the
+// current one's MMAs end); warps 3-6 stage the b digits of a tile and build its
+// Hankel slots ahead of the MMAs; warps 7-14 read an accumulator back and
+// reduce it while the next tile accumulates into the other one.  The roles
+// hand over through mbarriers only.
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     int batch, const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
     const uint32_t* __restrict__ b_data, const int64_t* __restrict__ b_off,
@@ -337,7 +367,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
 
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            mbar_init(bar(BAR_STAGE_FULL + i), 1);
+            mbar_init(bar(BAR_A_FULL + i), 1);
             mbar_init(bar(BAR_STAGE_EMPTY + i), 1);
             mbar_init(bar(BAR_ACC_FULL + i), 2);
             mbar_init(bar(BAR_ACC_EMPTY + i), EPI_WARPS);
@@ -366,13 +396,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
         uint32_t G = 0;  // Hankel groups consumed
         for (int k = 0;; ++k) {
             const int sb = k & 1;
-            int ok = 1;
-            if (lane == 0) {
-                ok = wait_parity(bar(BAR_STAGE_FULL + sb), (k >> 1) & 1);
-                if (ok && k >= 2) ok = wait_parity(bar(BAR_ACC_EMPTY + sb), ((k >> 1) - 1) & 1);
-                if (!ok) fail();
+            int ok = warp_wait(bar(BAR_A_FULL + sb), (k >> 1) & 1, lane);
+            if (ok && k >= 2) ok = warp_wait(bar(BAR_ACC_EMPTY + sb), ((k >> 1) - 1) & 1, lane);
+            if (!ok) {
+                if (lane == 0) fail();
+                break;
             }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             const TcTile tt = s_tiles[sb];
             if (lane == 0) {
                 s_epi[sb] = EpiInfo{tt.c, tt.L, tt.I0, tt.done};
@@ -395,12 +424,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                         const int nds = min(GROUP_D, tt.nd - gi * GROUP_D);
                         const int dg = tt.d_lo + gi * GROUP_D;
                         for (int s = 0; s < nds; ++s) {
-                            const uint32_t b_addr = sBa + (uint32_t)(NA_LIMB * (tt.d_hi - dg - s) * 16);
+                            const int d = dg + s;
+                            // columns of the output blocks this shift meets (a block I0 + lb with
+                            // 0 <= I0 + lb - d < na), widened to multiples of 16; the tile's first
+                            // shift spans all 240 columns and clears the accumulator
+                            uint32_t c0 = 0, nc = MMA_N;
+                            if (gi != 0 || s != 0) {
+                                const int lb0 = max(0, d - tt.I0), lb1 = min(NBLK - 1, d + tt.na - 1 - tt.I0);
+                                c0 = (uint32_t)(NA_LIMB * lb0) & ~15u;
+                                nc = min((uint32_t)MMA_N, (uint32_t)(NA_LIMB * lb1 + NA_LIMB + 15) & ~15u) - c0;
+                            }
+                            const uint32_t idesc = idesc_n(nc);
+                            const uint32_t b_addr = sBa + (uint32_t)((NA_LIMB * (tt.d_hi - d) + (int)c0) * 16);
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 const uint64_t da = smem_desc(ha + (uint32_t)((4 * s + 2 * h) * 512), 512, 128);
                                 const uint64_t db = smem_desc(b_addr + 2 * h * B_LBO, B_LBO, 128);
-                                mma_bf16(tacc, da, db, (gi == 0 && s == 0 && h == 0) ? 0u : 1u);
+                                mma_bf16(tacc + c0, da, db, idesc, (gi == 0 && s == 0 && h == 0) ? 0u : 1u);
                             }
                         }
                         mma_commit(bar(BAR_H_EMPTY + slot));
@@ -420,42 +460,61 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             if (!wait_parity(bar(BAR_DRAIN), 0)) fail();
         }
         __syncwarp();
-    } else if (warp < EPI_WARP0) {
-        // ---------------- producers ----------------
-        const int ptid = tid - 32 * PROD_WARP0;
-        uint32_t G = 0;  // Hankel groups built
+    } else if (warp < BLD_WARP0) {
+        // ---------------- stagers: claim tiles, a operand ----------------
+        const int stid = tid - 32 * STG_WARP0;
         for (int k = 0;; ++k) {
             const int sb = k & 1;
-            if (ptid == 0) {
+            if (stid == 0) {
                 bool stop = *s_abort != 0;
-                const int64_t tile = stop ? total : (int64_t)atomicAdd(counter, 1u);
                 if (!stop && k >= 2 && !wait_parity(bar(BAR_STAGE_EMPTY + sb), ((k >> 1) - 1) & 1)) {
                     fail();
                     stop = true;
                 }
+                const int64_t tile = stop ? total : (int64_t)atomicAdd(counter, 1u);
                 TcTile tt{};
-                if (!stop && tile < total)
+                if (tile < total)
                     tt = make_tile(tile, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
                 else
                     tt.done = 1;
                 s_tiles[sb] = tt;
             }
-            producers_sync();
+            stagers_sync();
             const TcTile tt = s_tiles[sb];
-            if (tt.done) {
-                if (ptid == 0) mbar_arrive(bar(BAR_STAGE_FULL + sb));
-                break;
+            if (!tt.done) {
+                stage_a(tt, sm + SM_B + sb * B_BUF, stid, tp.p);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                stagers_sync();
             }
-            stage_a(tt, sm + SM_B + sb * B_BUF, ptid, tp.p);
-            stage_b(tt, sbd, ptid, tp.p);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            producers_sync();
-            if (ptid == 0) mbar_arrive(bar(BAR_STAGE_FULL + sb));
+            if (stid == 0) mbar_arrive(bar(BAR_A_FULL + sb));
+            if (tt.done) break;
+        }
+    } else if (warp < EPI_WARP0) {
+        // ---------------- builders: b digits, Hankel slots ----------------
+        const int btid = tid - 32 * BLD_WARP0;
+        uint32_t G = 0;  // Hankel groups built
+        for (int k = 0;; ++k) {
+            const int sb = k & 1;
+            if (btid == 0) {
+                bool stop = *s_abort != 0;
+                if (!stop && !wait_parity(bar(BAR_A_FULL + sb), (k >> 1) & 1)) {
+                    fail();
+                    stop = true;
+                }
+                *s_pstop = stop;
+            }
+            builders_sync();
+            if (*s_pstop) break;
+            wait_parity(bar(BAR_A_FULL + sb), (k >> 1) & 1);  // completed: acquires the tile record
+            const TcTile tt = s_tiles[sb];
+            if (tt.done) break;
+            stage_b(tt, sbd, btid, tp.p);
             const int ngroups = (tt.nd + GROUP_D - 1) / GROUP_D;
             bool stop = false;
             for (int gi = 0; gi < ngroups; ++gi, ++G) {
                 const int slot = (int)(G % NH);
-                if (ptid == 0) {
+                builders_sync();  // (the b digits are complete before the first slot)
+                if (btid == 0) {
                     bool st = *s_abort != 0;
                     if (!st && G >= NH && !wait_parity(bar(BAR_H_EMPTY + slot), ((G / NH) - 1) & 1)) {
                         fail();
@@ -463,18 +522,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                     }
                     *s_pstop = st;
                 }
-                producers_sync();
+                builders_sync();
                 if (*s_pstop) {
                     stop = true;
                     break;
                 }
                 build_hankel(sbd, sm + SM_H + slot * H_SLOT, min(GROUP_D, tt.nd - gi * GROUP_D),
-                             tt.d_lo + gi * GROUP_D, tt.tb0, ptid);
+                             tt.d_lo + gi * GROUP_D, tt.tb0, btid);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                producers_sync();
-                if (ptid == 0) mbar_arrive(bar(BAR_H_FULL + slot));
+                builders_sync();
+                if (btid == 0) mbar_arrive(bar(BAR_H_FULL + slot));
             }
             if (stop) break;
+            builders_sync();  // every builder is past the last slot before the b digits change
         }
     } else {
         // ---------------- epilogue ----------------
@@ -488,12 +548,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
         const uint32_t whi = j == 0 ? tp.whi[0] : j == 1 ? tp.whi[1] : j == 2 ? tp.whi[2] : tp.whi[3];
         for (int k = 0;; ++k) {
             const int ab = k & 1;
-            int ok = 1;
-            if (lane == 0) {
-                ok = wait_parity(bar(BAR_ACC_FULL + ab), (k >> 1) & 1);
-                if (!ok) fail();
+            if (!warp_wait(bar(BAR_ACC_FULL + ab), (k >> 1) & 1, lane)) {
+                if (lane == 0) fail();
+                break;
             }
-            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             const EpiInfo info = s_epi[ab];
             if (info.done) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

@@ -41,6 +41,17 @@ def test_equal_degrees(deg):
     assert_equal(run(packed, deg), oracle.polymul_batch(*packed[:4], packed[4], P), f"deg {deg}")
 
 
+def test_random_unequal_pairs():
+    """Degrees drawn independently in [0, 4095]: the per-shift column windows start and end
+    at every offset within a tile."""
+    rng = np.random.default_rng(1402)
+    da = rng.integers(0, 4096, 96).astype(np.int64)
+    db = rng.integers(0, 4096, 96).astype(np.int64)
+    da[:4] = [4095, 0, 31, 4095]; db[:4] = [100, 4095, 4064, 32]
+    packed = inputs.packed_batch(da, db, 92)
+    assert_equal(run(packed, 4095), oracle.polymul_batch(*packed[:4], packed[4], P))
+
+
 def _adversarial_values(p):
     """Coefficients whose balanced digits are all at the extreme (-128 for b, -32 for a)."""
     xb = p - 128 * (1 + 256 + 65536)        # digits (-128, -128, -128, 0) in base 256
