@@ -47,6 +47,7 @@ constexpr int WB = PM_WB;        // warps per CTA, all on one output tile
 constexpr int NT = 32 * WB;      // threads per CTA
 constexpr int CHUNK_MAX = 2048;  // b coefficients staged per chunk (two chunks in flight)
 constexpr int FRONT = 8;         // a-window words before index 0 (read by the last prefetch)
+constexpr int FIRST_CHUNK = 512; // a CTA's very first chunk: short, so that its products start early
 
 // Build-time tuning knobs (defaults chosen by measurement on GB300).
 #ifndef PM_MINB
@@ -105,37 +106,39 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Chunk `ci` of the b-range [jb0, jb1): start, length and padded length CL
-// (a multiple of KB).  Warp w takes sub-steps [first, first + count) of the
-// CL / KB sub-steps, the counts differing by at most one.
+// Chunk `ci` of the b-range [jb0, jb1), whose chunk 0 holds f coefficients
+// and the others CHUNK_MAX: start, length and padded length CL (a multiple of
+// KB).  Warp w takes sub-steps [first, first + count) of the CL / KB
+// sub-steps, the counts differing by at most one.
 struct ChunkDims {
     int jc, clen, CL;
 };
-template <int KB>
-__device__ __forceinline__ ChunkDims chunk_dims(int jb0, int jb1, int ci) {
+template <int KB, int CH = CHUNK_MAX>
+__device__ __forceinline__ ChunkDims chunk_dims(int jb0, int jb1, int ci, int f) {
     ChunkDims c;
-    c.jc = jb0 + ci * CHUNK_MAX;
-    c.clen = min(CHUNK_MAX, jb1 - c.jc);
+    c.jc = jb0 + (ci == 0 ? 0 : f + (ci - 1) * CH);
+    c.clen = min(ci == 0 ? f : CH, jb1 - c.jc);
     c.CL = (c.clen + KB - 1) / KB * KB;
     return c;
 }
 
 // Issues the copies of one chunk: b[jc .. jc+clen) (zeros up to CL) and the
-// a-window a[d0-(jc+CL-1) .. d0+TD-jc) (zeros outside [0, n)).
-template <int S>
+// a-window a[d0-(jc+CL-1) .. d0+TD-jc) (zeros outside [0, n)), by threads
+// tid, tid + nthr, ... of the group that stages (AW = a-window words).
+template <int S, int AW>
 __device__ __forceinline__ void stage_chunk(const uint32_t* __restrict__ a, int n,
                                             const uint32_t* __restrict__ b, int d0,
-                                            const ChunkDims& ch, uint32_t* buf) {
+                                            const ChunkDims& ch, uint32_t* buf, int tid, int nthr) {
     using C = Cfg<S>;
     uint32_t* sA = buf;
-    uint32_t* sB = buf + C::A_WORDS;
-    for (int i = threadIdx.x; i < ch.CL; i += NT) {
+    uint32_t* sB = buf + AW;
+    for (int i = tid; i < ch.CL; i += nthr) {
         const bool v = i < ch.clen;
         cp_async4(sB + i, b + (v ? ch.jc + i : 0), v);
     }
     const int abase = d0 - (ch.jc + ch.CL - 1);
     const int alen = C::TD + ch.CL - 1;
-    for (int i = threadIdx.x; i < alen; i += NT) {
+    for (int i = tid; i < alen; i += nthr) {
         const int ai = abase + i;
         const bool v = ai >= 0 && ai < n;
         cp_async4(sA + a_phys(FRONT + i), a + (v ? ai : 0), v);
@@ -163,16 +166,17 @@ __device__ __forceinline__ void load_group(const uint32_t* sA, int base, uint32_
 
 // Multiplication phase of one staged chunk (CL coefficients of b and the
 // a-window they meet): acc[e] += sum over the chunk of a[d - j] b[j] for
-// d = d0 + S*lane + e.  Values stay congruent mod p and below 2^64 (see
+// d = d0 + S*lane + e, over the share of warp `warp` of the nw warps that
+// split the chunk.  Values stay congruent mod p and below 2^64 (see
 // ModParams); fold_ctr counts sub-steps since the last fold.
 template <int S>
 __device__ __forceinline__ void compute_chunk(const uint32_t* sA, const uint32_t* sB, int CL,
-                                              const ModParams& mp, uint64_t (&acc)[S], int& fold_ctr) {
+                                              const ModParams& mp, uint64_t (&acc)[S], int& fold_ctr,
+                                              int warp, int nw) {
     using C = Cfg<S>;
     constexpr int KB = C::KB, NGW = C::NGW, R = C::R;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int tot = CL / KB, qw = tot / WB, rw = tot % WB;
+    const int tot = CL / KB, qw = tot / nw, rw = tot % nw;
     const int nsub = qw + (warp < rw ? 1 : 0);
     const int r0 = KB * (warp * qw + min(warp, rw));
     int base = S * lane + CL - KB - r0;  // window index of group 0 at the current sub-step
@@ -295,13 +299,14 @@ struct Seg {
     int n, m;              // n >= m (the longer operand slides through the window)
     int d0;                // first output of the tile
     int jb0, jb1;          // coefficients of b of this segment
+    int f;                 // coefficients in chunk 0
     int nchunks;
     int64_t x, x_end, s_tile, e_tile;  // positions
 };
 
 // Walks a CTA's segments in order: pi = current pair, t = tile of the last
 // segment in it (-1: not known, search).
-template <int S, bool BATCH>
+template <int S, bool BATCH, int CH = CHUNK_MAX>
 __device__ __forceinline__ Seg make_seg(int64_t x, int64_t x1, int& pi, int64_t& t,
                                         const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
                                         const uint32_t* __restrict__ b_data, const int64_t* __restrict__ b_off,
@@ -345,7 +350,8 @@ __device__ __forceinline__ Seg make_seg(int64_t x, int64_t x1, int& pi, int64_t&
     sg.d0 = (int)(t * C::TD);
     sg.jb0 = (int)(jlo + (x - sg.s_tile));
     sg.jb1 = (int)(jlo + (sg.x_end - sg.s_tile));
-    sg.nchunks = (sg.jb1 - sg.jb0 + CHUNK_MAX - 1) / CHUNK_MAX;
+    sg.f = CH;
+    sg.nchunks = (sg.jb1 - sg.jb0 + CH - 1) / CH;
     if (t + 1 == nt) t = -1;  // the pair ends with this tile
     return sg;
 }
@@ -369,20 +375,32 @@ __device__ __forceinline__ void finish_segment(const Seg& sg, uint64_t (&acc)[S]
     const int64_t slot = 2 * k + (sg.x == x0 ? 0 : 1);
     uint32_t* mine = sk.slots + slot * C::TD;
     for (int o = threadIdx.x; o < C::TD; o += NT) mine[o] = sm.red[o];
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        // the barrier orders every thread's slot writes before this fence, and a
+        // fence orders what its thread has observed: the slot is visible before
+        // the count is
+        __threadfence();
         const unsigned int seen = atomicAdd(&sk.counters[k1], 1u);
-        *s_last = (seen == (unsigned int)(k2 - k1)) ? 1 : 0;
+        const int last = seen == (unsigned int)(k2 - k1) ? 1 : 0;
+        if (last) __threadfence();  // and the other contributors' slots before the reads below
+        *s_last = last;
     }
     __syncthreads();
     if (*s_last) {  // every other contributor has written its slot
-        __threadfence();
         const int64_t first_slot = 2 * k1 + (sp.start(k1) == sg.s_tile ? 0 : 1);
         for (int o = threadIdx.x; o < C::TD; o += NT) {
-            uint64_t sum = __ldcg(sk.slots + first_slot * C::TD + o);
-            for (int64_t kk = k1 + 1; kk <= k2; ++kk) sum += __ldcg(sk.slots + 2 * kk * C::TD + o);
-            if (sg.d0 + o < L) sg.c[sg.d0 + o] = barrett(sum, mp.p, mp.mu);
+            // four independent sums keep several L2 reads in flight
+            uint64_t s0 = __ldcg(sk.slots + first_slot * C::TD + o), s1 = 0, s2 = 0, s3 = 0;
+            int64_t kk = k1 + 1;
+            for (; kk + 3 <= k2; kk += 4) {
+                s0 += __ldcg(sk.slots + 2 * kk * C::TD + o);
+                s1 += __ldcg(sk.slots + 2 * (kk + 1) * C::TD + o);
+                s2 += __ldcg(sk.slots + 2 * (kk + 2) * C::TD + o);
+                s3 += __ldcg(sk.slots + 2 * (kk + 3) * C::TD + o);
+            }
+            for (; kk <= k2; ++kk) s0 += __ldcg(sk.slots + 2 * kk * C::TD + o);
+            if (sg.d0 + o < L) sg.c[sg.d0 + o] = barrett(s0 + s1 + s2 + s3, mp.p, mp.mu);
         }
         if (threadIdx.x == 0) sk.counters[k1] = 0;
     }
@@ -432,7 +450,12 @@ __global__ void PM_BOUNDS plain_sk_kernel(
     Seg cur = make_seg<S, BATCH>(x0, x1, pi, t, a_data, a_off, b_data, b_off, c_data, c_off, n1, m1, prefix);
     int ci = 0, bi = 0, fold_ctr = 0;
     uint64_t acc[S];
-    stage_chunk<S>(cur.a, cur.n, cur.b, cur.d0, chunk_dims<KB>(cur.jb0, cur.jb1, 0), sm.buf);
+    if (cur.jb1 - cur.jb0 > FIRST_CHUNK) {
+        cur.f = FIRST_CHUNK;
+        cur.nchunks = 1 + (cur.jb1 - cur.jb0 - FIRST_CHUNK + CHUNK_MAX - 1) / CHUNK_MAX;
+    }
+    stage_chunk<S, C::A_WORDS>(cur.a, cur.n, cur.b, cur.d0, chunk_dims<KB>(cur.jb0, cur.jb1, 0, cur.f), sm.buf,
+                               threadIdx.x, NT);
     for (;;) {
         Seg nxt = cur;
         int nci = ci + 1;
@@ -447,8 +470,8 @@ __global__ void PM_BOUNDS plain_sk_kernel(
             }
         }
         if (has_next) {  // the next chunk streams in while this one is used
-            stage_chunk<S>(nxt.a, nxt.n, nxt.b, nxt.d0, chunk_dims<KB>(nxt.jb0, nxt.jb1, nci),
-                           sm.buf + (bi ^ 1) * C::BUF_WORDS);
+            stage_chunk<S, C::A_WORDS>(nxt.a, nxt.n, nxt.b, nxt.d0, chunk_dims<KB>(nxt.jb0, nxt.jb1, nci, nxt.f),
+                                       sm.buf + (bi ^ 1) * C::BUF_WORDS, threadIdx.x, NT);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -460,7 +483,8 @@ __global__ void PM_BOUNDS plain_sk_kernel(
             fold_ctr = 0;
         }
         const uint32_t* sA = sm.buf + bi * C::BUF_WORDS;
-        compute_chunk<S>(sA, sA + C::A_WORDS, chunk_dims<KB>(cur.jb0, cur.jb1, ci).CL, mp, acc, fold_ctr);
+        compute_chunk<S>(sA, sA + C::A_WORDS, chunk_dims<KB>(cur.jb0, cur.jb1, ci, cur.f).CL, mp, acc, fold_ctr,
+                         threadIdx.x >> 5, WB);
         __syncthreads();  // this buffer is refilled by the next staging
         if (ci == cur.nchunks - 1) finish_segment<S>(cur, acc, mp, sm, sp, k, x0, sk, &s_last);
         if (!has_next) break;
@@ -469,6 +493,220 @@ __global__ void PM_BOUNDS plain_sk_kernel(
         bi ^= 1;
     }
 }
+
+// ---------------------------------------------------------------------------
+// Warp-level form, for batches of small pairs.  The same positions and the
+// same inner loop, but the unit of work belongs to a warp instead of a CTA,
+// and warps claim units from a counter (one ahead of the unit they work on),
+// so that warps the scheduler serves faster take more of them and the SMs
+// finish together.  A unit is a whole pair when the pair has at most Q
+// positions (all its tiles are then written directly), else one of the
+// ceil(positions / Q) pieces of Q positions of the pair; only those pieces
+// cut tiles, and a cut tile goes through the partial-sum slots of its pieces
+// and the counter of its first piece as in the CTA form.  Units are claimed
+// in three tiers, pieces first, then whole pairs of at least Q / 8 positions,
+// then the rest, so that the last units handed out are small.  Q is set on the
+// device from the total number of positions.  A warp stages its own chunks
+// (double-buffered, WK_CHUNK coefficients of b) and keeps its own sums; no
+// CTA-wide barrier remains.
+// ---------------------------------------------------------------------------
+constexpr int WK_WARPS = 8;           // independent warps per CTA
+constexpr int WK_CHUNK = 256;         // b coefficients per warp chunk
+constexpr int64_t WK_MIN_UNIT = 256;  // positions per piece, at least
+constexpr int64_t WK_MAX_DEG = 4095;  // batches whose degrees stay below take this form
+// pieces at most (two slots of TD words each per piece: 64 MiB for TD <= 256)
+__host__ __device__ constexpr int64_t wk_units_max(int td) { return td <= 256 ? 32768 : 8 * 1024 * 1024 / td; }
+
+// Schedule of the warp-level form, written by its planner.
+struct WkPlan {
+    int64_t* pos;        // [batch + 1] positions before pair i (as in the CTA form)
+    int64_t* kbase;      // [batch + 1] pieces before pair i
+    int64_t* rank;       // [batch] place of a whole pair within its tier (-1: the pair is cut in pieces)
+    int64_t* bsum;       // [batch / 256] position sums of the count kernel's blocks
+    int* unit_pair;      // [units] the pair of each unit, in claim order
+    int64_t* sched;      // Q, units of tiers 0..2, claim counter
+};
+
+template <int S>
+struct WCfg {
+    static constexpr int TD = 32 * S;
+    static constexpr int A_LOGICAL = FRONT + TD + WK_CHUNK + 8;
+    static constexpr int A_CHUNKS = (A_LOGICAL + 3) / 4;
+    static constexpr int A_WORDS = 4 * (A_CHUNKS + A_CHUNKS / 8 + 2);
+    static constexpr int BUF_WORDS = A_WORDS + WK_CHUNK;
+    static constexpr size_t SMEM = 4 * (size_t)WK_WARPS * 2 * BUF_WORDS;
+};
+
+// A warp's finished segment: its sums reduced mod p, then the tile's outputs
+// or the piece's partial-sum slot.  Positions here are relative to the pair;
+// piece v covers [v Q, v Q + Q) and the pair's pieces are numbered from kbase.
+template <int S>
+__device__ __forceinline__ void warp_finish(const Seg& sg, uint64_t (&acc)[S], const ModParams& mp, int64_t kbase,
+                                            int64_t v, int64_t y0, int64_t Q, int64_t pbase, SkScratch sk) {
+    constexpr int TD = 32 * S;
+    const int lane = threadIdx.x & 31;
+    const int L = sg.n + sg.m - 1;
+    const int o0 = S * lane;
+    uint32_t r[S];
+#pragma unroll
+    for (int e = 0; e < S; ++e) r[e] = barrett(fold2(acc[e], mp.c32), mp.p, mp.mu);
+    if (sg.x == sg.s_tile && sg.x_end == sg.e_tile) {
+#pragma unroll
+        for (int e = 0; e < S; ++e)
+            if (sg.d0 + o0 + e < L) sg.c[sg.d0 + o0 + e] = r[e];
+        return;
+    }
+    // a cut tile (only pieces cut tiles): this piece's part goes to its slot (0
+    // for the segment that starts the piece, 1 for the one that ends it); the
+    // piece that arrives last at the counter of the tile's first piece adds
+    // the parts, writes the outputs and resets the counter
+    const int64_t ys = sg.s_tile - pbase, ye = sg.e_tile - pbase;
+    const int64_t k1 = kbase + ys / Q, k2 = kbase + (ye - 1) / Q;
+    uint32_t* mine = sk.slots + (2 * (kbase + v) + (sg.x - pbase == y0 ? 0 : 1)) * TD;
+#pragma unroll
+    for (int e = 0; e < S; ++e) mine[o0 + e] = r[e];
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) {
+        __threadfence();  // the warp's slot (ordered before by the warp barrier) before the count
+        const unsigned int seen = atomicAdd(&sk.counters[k1], 1u);
+        last = seen == (unsigned int)(k2 - k1) ? 1 : 0;
+        if (last) __threadfence();
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    __syncwarp();
+    if (last) {
+        uint64_t sa[S], sb[S];
+        const uint32_t* first = sk.slots + (2 * k1 + ((k1 - kbase) * Q == ys ? 0 : 1)) * TD + o0;
+#pragma unroll
+        for (int e = 0; e < S; ++e) { sa[e] = __ldcg(first + e); sb[e] = 0; }
+        int64_t kk = k1 + 1;
+        for (; kk + 1 <= k2; kk += 2) {  // two slots' reads in flight at a time
+            const uint32_t* s0 = sk.slots + 2 * kk * TD + o0;
+            const uint32_t* s1 = s0 + 2 * TD;
+#pragma unroll
+            for (int e = 0; e < S; ++e) { sa[e] += __ldcg(s0 + e); sb[e] += __ldcg(s1 + e); }
+        }
+        if (kk <= k2) {
+#pragma unroll
+            for (int e = 0; e < S; ++e) sa[e] += __ldcg(sk.slots + 2 * kk * TD + o0 + e);
+        }
+#pragma unroll
+        for (int e = 0; e < S; ++e)
+            if (sg.d0 + o0 + e < L) sg.c[sg.d0 + o0 + e] = barrett(sa[e] + sb[e], mp.p, mp.mu);
+        if (lane == 0) sk.counters[k1] = 0;
+    }
+}
+
+// Where a unit lies: pair i, its piece v (0 for a whole pair), the pair's
+// first piece number kbase (pieces only) and its relative positions [y0, y1).
+struct WkUnit {
+    int i;
+    int64_t v, kbase, y0, y1;
+};
+
+__device__ __forceinline__ WkUnit wk_decode(int64_t u, const WkPlan& pl, int64_t Q, int64_t tot0) {
+    WkUnit w;
+    w.i = pl.unit_pair[u];
+    const int64_t npos = pl.pos[w.i + 1] - pl.pos[w.i];
+    w.kbase = pl.kbase[w.i];
+    const bool piece = u < tot0;
+    w.v = piece ? u - w.kbase : 0;
+    w.y0 = piece ? w.v * Q : 0;
+    w.y1 = piece ? min(w.y0 + Q, npos) : npos;
+    return w;
+}
+
+template <int S>
+__global__ void __launch_bounds__(32 * WK_WARPS) plain_warp_kernel(
+    const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
+    const uint32_t* __restrict__ b_data, const int64_t* __restrict__ b_off,
+    uint32_t* __restrict__ c_data, const int64_t* __restrict__ c_off, int batch, WkPlan pl, ModParams mp,
+    SkScratch sk) {
+    using W = WCfg<S>;
+    constexpr int KB = Cfg<S>::KB;
+    extern __shared__ uint4 smem_raw[];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    uint32_t* buf = reinterpret_cast<uint32_t*>(smem_raw) + wi * 2 * W::BUF_WORDS;
+    const int64_t Q = pl.sched[0];
+    const int64_t tot0 = pl.sched[1];
+    const int64_t U = tot0 + pl.sched[2] + pl.sched[3];
+    unsigned long long* claim = reinterpret_cast<unsigned long long*>(pl.sched + 4);
+    auto take = [&]() -> int64_t {
+        unsigned long long u = 0;
+        if (lane == 0) u = atomicAdd(claim, 1ull);
+        return (int64_t)__shfl_sync(0xffffffffu, u, 0);
+    };
+    int64_t u = take();
+    if (u >= U) return;  // (no CTA-wide barrier follows)
+    int64_t u_next = take();  // claimed one ahead
+    // the claim after that is issued at once and read at the next switch, so
+    // that the atomic's round trip overlaps this unit's work
+    unsigned long long pending = 0;
+    if (lane == 0) pending = atomicAdd(claim, 1ull);
+    WkUnit w = wk_decode(u, pl, Q, tot0);
+    int pi = w.i;
+    int64_t t = -1;
+    Seg cur = make_seg<S, true, WK_CHUNK>(pl.pos[pi] + w.y0, pl.pos[pi] + w.y1, pi, t, a_data, a_off, b_data, b_off,
+                                         c_data, c_off, 0, 0, pl.pos);
+    int ci = 0, bi = 0, fold_ctr = 0;
+    uint64_t acc[S];
+    stage_chunk<S, W::A_WORDS>(cur.a, cur.n, cur.b, cur.d0, chunk_dims<KB, WK_CHUNK>(cur.jb0, cur.jb1, 0, cur.f),
+                               buf, lane, 32);
+    for (;;) {
+        // the chunk after this one: of this segment, of the unit's next segment, or of the next unit
+        Seg nxt = cur;
+        int nci = ci + 1;
+        WkUnit nw = w;
+        bool has_next = true, new_unit = false;
+        if (nci >= cur.nchunks) {
+            nci = 0;
+            if (cur.x_end < pl.pos[w.i] + w.y1) {
+                nxt = make_seg<S, true, WK_CHUNK>(cur.x_end, pl.pos[w.i] + w.y1, pi, t, a_data, a_off, b_data, b_off,
+                                                  c_data, c_off, 0, 0, pl.pos);
+            } else if (u_next < U) {
+                nw = wk_decode(u_next, pl, Q, tot0);
+                new_unit = true;
+                pi = nw.i;
+                t = -1;
+                nxt = make_seg<S, true, WK_CHUNK>(pl.pos[pi] + nw.y0, pl.pos[pi] + nw.y1, pi, t, a_data, a_off,
+                                                  b_data, b_off, c_data, c_off, 0, 0, pl.pos);
+            } else {
+                has_next = false;
+            }
+        }
+        if (has_next) {
+            stage_chunk<S, W::A_WORDS>(nxt.a, nxt.n, nxt.b, nxt.d0,
+                                       chunk_dims<KB, WK_CHUNK>(nxt.jb0, nxt.jb1, nci, nxt.f),
+                                       buf + (bi ^ 1) * W::BUF_WORDS, lane, 32);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        if (ci == 0) {
+#pragma unroll
+            for (int e = 0; e < S; ++e) acc[e] = 0;
+            fold_ctr = 0;
+        }
+        const uint32_t* sA = buf + bi * W::BUF_WORDS;
+        compute_chunk<S>(sA, sA + W::A_WORDS, chunk_dims<KB, WK_CHUNK>(cur.jb0, cur.jb1, ci, cur.f).CL, mp, acc,
+                         fold_ctr, 0, 1);
+        __syncwarp();  // this buffer is refilled by the next staging
+        if (ci == cur.nchunks - 1) warp_finish<S>(cur, acc, mp, w.kbase, w.v, w.y0, Q, pl.pos[w.i], sk);
+        if (!has_next) break;
+        if (new_unit) {  // moving to the claimed unit: the next claim is the pending one
+            w = nw;
+            u = u_next;
+            u_next = (int64_t)__shfl_sync(0xffffffffu, pending, 0);
+            if (lane == 0) pending = atomicAdd(claim, 1ull);
+        }
+        cur = nxt;
+        ci = nci;
+        bi ^= 1;
+    }
+}
+
 
 // ---------------------------------------------------------------------------
 // Batched form: a planner kernel validates the CSR layout and computes the
@@ -533,6 +771,174 @@ __global__ void __launch_bounds__(PLAN_THREADS) batch_plan_kernel(
     if (tid == PLAN_THREADS - 1) prefix[batch] = s_scan[PLAN_THREADS - 1];
 }
 
+// inclusive scan of one value per thread over the block
+__device__ __forceinline__ long long block_scan(long long v, long long* sh) {
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int off = 1; off < PLAN_THREADS; off <<= 1) {
+        const long long w = tid >= off ? sh[tid - off] : 0;
+        __syncthreads();
+        sh[tid] += w;
+        __syncthreads();
+    }
+    const long long r = sh[tid];
+    __syncthreads();
+    return r;
+}
+
+// Planner of the warp-level form, in three kernels.  warp_count_kernel (one
+// thread per pair): the pair's position count in pos[i] (-1 for a pair that
+// fails the checks of batch_plan_kernel) and each block's sum in bsum.
+// warp_plan_kernel (one CTA, only scans): Q from the total, the prefix of
+// positions (in place), the pieces before each pair (kbase), each pair's place
+// in the claim order (rank) and the three tiers' sizes.  warp_fill_kernel (one
+// warp per pair): the table of the pair of every unit; it also resets the
+// claim counter.
+__global__ void __launch_bounds__(256) warp_count_kernel(int batch, const int64_t* __restrict__ a_off,
+                                                         const int64_t* __restrict__ b_off,
+                                                         const int64_t* __restrict__ c_off, int64_t max_deg, int td,
+                                                         int64_t* __restrict__ pos, int64_t* __restrict__ bsum) {
+    __shared__ long long s_sum[8];
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    int64_t np = 0;
+    if (i < batch) {
+        int64_t n, m;
+        np = pair_dims(i, a_off, b_off, c_off, max_deg, &n, &m) ? pair_positions(n, m, td) : -1;
+        pos[i] = np;
+    }
+    long long v = np > 0 ? np : 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < 8; ++w) t += s_sum[w];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+__device__ __forceinline__ int64_t div_up(int64_t x, int64_t q) {
+    return (x < 0x7fffffff && q < 0x7fffffff) ? (int64_t)(((uint32_t)x + (uint32_t)q - 1) / (uint32_t)q)
+                                               : (x + q - 1) / q;
+}
+
+// Inclusive scan over the block of three values per thread, by warp shuffles
+// (two barriers); sh holds 3 x 32 words.
+__device__ __forceinline__ void block_scan3(long long& x0, long long& x1, long long& x2, long long* sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long y0 = __shfl_up_sync(0xffffffffu, x0, off);
+        const long long y1 = __shfl_up_sync(0xffffffffu, x1, off);
+        const long long y2 = __shfl_up_sync(0xffffffffu, x2, off);
+        if (lane >= off) { x0 += y0; x1 += y1; x2 += y2; }
+    }
+    if (lane == 31) { sh[w] = x0; sh[32 + w] = x1; sh[64 + w] = x2; }
+    __syncthreads();
+    if (w == 0) {
+        long long t0 = sh[lane], t1 = sh[32 + lane], t2 = sh[64 + lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long y0 = __shfl_up_sync(0xffffffffu, t0, off);
+            const long long y1 = __shfl_up_sync(0xffffffffu, t1, off);
+            const long long y2 = __shfl_up_sync(0xffffffffu, t2, off);
+            if (lane >= off) { t0 += y0; t1 += y1; t2 += y2; }
+        }
+        sh[lane] = t0; sh[32 + lane] = t1; sh[64 + lane] = t2;
+    }
+    __syncthreads();
+    if (w > 0) { x0 += sh[w - 1]; x1 += sh[32 + w - 1]; x2 += sh[64 + w - 1]; }
+    __syncthreads();  // sh is free again
+}
+
+__global__ void __launch_bounds__(PLAN_THREADS) warp_plan_kernel(int batch, int td, WkPlan pl, int* status) {
+    // pairs in rounds of PLAN_THREADS, pair r PLAN_THREADS + tid by thread tid
+    __shared__ long long s_scan[96];
+    __shared__ int s_bad;
+    __shared__ long long s_round[4];
+    const int tid = threadIdx.x;
+    const int rounds = (batch + PLAN_THREADS - 1) / PLAN_THREADS;
+    __shared__ long long s_g;
+    {
+        long long t = 0;  // the count kernel's block sums
+        for (int bidx = tid; bidx < (batch + 255) / 256; bidx += PLAN_THREADS) t += pl.bsum[bidx];
+        long long d1 = 0, d2 = 0;
+        block_scan3(t, d1, d2, s_scan);
+        if (tid == PLAN_THREADS - 1) s_g = t;
+        __syncthreads();
+    }
+    const int64_t G = s_g;
+    const int64_t umax = wk_units_max(td);
+    // pieces cut only pairs of more than Q positions: at most 2 G / Q of them
+    const int64_t Q = max(WK_MIN_UNIT, (2 * G + umax - 1) / umax);
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    // running totals of positions, pieces, tier-1 and tier-2 pairs
+    long long bp = 0, b0 = 0, b1 = 0, b2 = 0;
+    int64_t np_next = tid < batch ? pl.pos[tid] : 0;
+    for (int r = 0; r < rounds; ++r) {
+        const int i = r * PLAN_THREADS + tid;
+        const int64_t np = np_next;
+        // the next round's count is read now, its latency behind this round's scans
+        // (this round overwrites only its own entries)
+        np_next = i + PLAN_THREADS < batch ? pl.pos[i + PLAN_THREADS] : 0;
+        if (np < 0) s_bad = 1;
+        const int tier = (i >= batch || np < 0) ? 3 : (np > Q ? 0 : (8 * np >= Q ? 1 : 2));
+        const long long nu = tier == 0 ? div_up(np, Q) : 0;
+        long long xp = np > 0 ? np : 0, x0 = nu, x1 = tier == 1;
+        block_scan3(xp, x0, x1, s_scan);
+        long long x2 = tier == 2, d1 = 0, d2 = 0;
+        block_scan3(x2, d1, d2, s_scan);
+        if (i < batch) {
+            pl.pos[i] = bp + xp - (np > 0 ? np : 0);  // the count becomes the prefix
+            pl.kbase[i] = b0 + x0 - nu;
+            // rank: the tier-1 or tier-2 table slot (relative to the tier), -1 for pieces
+            pl.rank[i] = tier == 1 ? b1 + x1 - 1 : (tier == 2 ? b2 + x2 - 1 : -1);
+        }
+        if (tid == PLAN_THREADS - 1) { s_round[0] = xp; s_round[1] = x0; s_round[2] = x1; s_round[3] = x2; }
+        __syncthreads();
+        bp += s_round[0];
+        b0 += s_round[1];
+        b1 += s_round[2];
+        b2 += s_round[3];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const bool bad = s_bad != 0;
+        if (bad) atomicCAS(status, 0, (int)PM_ERR_INVALID_ARG);
+        pl.pos[batch] = G;
+        pl.kbase[batch] = b0;
+        pl.sched[0] = Q;
+        pl.sched[1] = bad ? 0 : b0;  // nothing is computed for an invalid batch
+        pl.sched[2] = bad ? 0 : b1;
+        pl.sched[3] = bad ? 0 : b2;
+    }
+}
+
+// The unit table (claim order: pieces, tier 1, tier 2), one warp per pair.
+__global__ void __launch_bounds__(256) warp_fill_kernel(int batch, WkPlan pl) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        pl.sched[4] = 0;  // claim counter
+    }
+    if (i >= batch) return;
+    const int64_t tot0 = pl.sched[1], tot1 = pl.sched[2];
+    const int64_t rk = pl.rank[i];
+    if (rk >= 0) {
+        if (lane == 0) {
+            const int64_t np = pl.pos[i + 1] - pl.pos[i];
+            const int64_t Q = pl.sched[0];
+            pl.unit_pair[(8 * np >= Q ? tot0 : tot0 + tot1) + rk] = i;
+        }
+        return;
+    }
+    const int64_t k0 = pl.kbase[i], k1 = pl.kbase[i + 1];
+    for (int64_t k = k0 + lane; k < k1; k += 32) pl.unit_pair[k] = i;
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
@@ -557,10 +963,18 @@ static cudaError_t kernel_setup(K kern, size_t smem, int dev, int* cache, int* o
     return cudaSuccess;
 }
 
-// Scratch layout: COUNTER_MAX counters (zeroed when the buffer is allocated and
-// returned to zero by every call), then 2 P slots of TD words.
+// Scratch layout: COUNTER_REGION counters (zeroed when the buffer is allocated
+// and returned to zero by every call), then 2 P slots of TD words.  Both forms
+// keep their counters in this region (the CTA form one per CTA unit, at most
+// COUNTER_MAX; the warp-level form one per piece, at most wk_units_max), so
+// that a call of one form never finds the other's slots where it expects
+// counters.
 constexpr int64_t COUNTER_MAX = 4096;
-constexpr size_t COUNTER_BYTES = COUNTER_MAX * sizeof(unsigned int);
+constexpr int64_t COUNTER_REGION = 32768;
+constexpr size_t COUNTER_BYTES = COUNTER_REGION * sizeof(unsigned int);
+static_assert(wk_units_max(32) <= COUNTER_REGION && wk_units_max(256) <= COUNTER_REGION &&
+                  wk_units_max(512) <= COUNTER_REGION && COUNTER_MAX <= COUNTER_REGION,
+              "counters");
 
 static size_t sk_bytes(int64_t P, int td) {
     return COUNTER_BYTES + (size_t)(2 * P * td) * sizeof(uint32_t);
@@ -615,11 +1029,61 @@ pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t 
     }
 }
 
+// Warp-level form of the batched product (degrees below WK_MAX_DEG).
+template <int S>
+static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
+                                       const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
+                                       const int64_t* c_off, uint32_t p, int64_t max_deg,
+                                       cudaStream_t st, DeviceWorkspace* ws) {
+    using W = WCfg<S>;
+    auto kern = plain_warp_kernel<S>;
+    static int occ_cache[64] = {};
+    int occ = 0;
+    cudaError_t e = kernel_setup(kern, W::SMEM, ws->device, occ_cache, &occ, 32 * WK_WARPS);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int64_t grid = (int64_t)ws->num_sms * occ;
+    StreamScratch* sc = nullptr;
+    pm_status rc = stream_scratch(ws, st, &sc);
+    if (rc != PM_OK) return rc;
+    const int64_t umax = wk_units_max(W::TD);
+    rc = ensure_scratch(&sc->sk, &sc->sk_bytes, sk_bytes(umax, W::TD), st, /*zero=*/true);
+    if (rc != PM_OK) return rc;
+    // sched (8), pos, kbase (batch + 1 each), rank (batch), block sums, unit table (umax + batch ints)
+    const int64_t nblk = (batch + 255) / 256;
+    rc = ensure_scratch(&sc->plan, &sc->plan_bytes,
+                        sizeof(int64_t) * (size_t)(3 * batch + 2 + 8 + nblk) + sizeof(int) * (size_t)(umax + batch),
+                        st, false);
+    if (rc != PM_OK) return rc;
+    const SkScratch sk = sk_carve(sc->sk);
+    WkPlan pl;
+    pl.sched = reinterpret_cast<int64_t*>(sc->plan);
+    pl.pos = pl.sched + 8;
+    pl.kbase = pl.pos + (batch + 1);
+    pl.rank = pl.kbase + (batch + 1);
+    pl.bsum = pl.rank + batch;
+    pl.unit_pair = reinterpret_cast<int*>(pl.bsum + nblk);
+    warp_count_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg,
+                                                                      W::TD, pl.pos, pl.bsum);
+    warp_plan_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, W::TD, pl, ws->status);
+    warp_fill_kernel<<<(unsigned)((batch + 7) / 8), 256, 0, st>>>((int)batch, pl);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    const ModParams mp = host_mod_params(p, Cfg<S>::KB);
+    kern<<<(unsigned)grid, 32 * WK_WARPS, W::SMEM, st>>>(a_data, a_off, b_data, b_off, c_data, c_off, (int)batch, pl,
+                                                          mp, sk);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(4);
+    return PM_OK;
+}
+
 template <int S>
 static pm_status launch_batched_s(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                   const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                   const int64_t* c_off, uint32_t p, int64_t max_deg,
                                   cudaStream_t st, DeviceWorkspace* ws) {
+    if (max_deg <= WK_MAX_DEG && S <= 32)  // (64 sums per lane would spill in the warp form)
+        return launch_batched_warp_s<S>(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, st, ws);
     using C = Cfg<S>;
     auto kern = plain_sk_kernel<S, true>;
     static int occ_cache[64] = {};

@@ -19,8 +19,7 @@
 // the K index runs backwards, k' = 31 - k, in both operands):
 //     D[(j, r)][(I, i)] = sum_delta sum_{k'<32} d_j[32 delta - 31 + r + k'] * e_i[32 (I - delta) + 31 - k']
 //                       = (e_i * d_j)[32 I + r].
-// For one shift delta this is one 128 x 240 x 32 product (two MMAs of K = 16),
-// narrowed after the tile's first shift to the columns whose a block exists:
+// For one shift delta this is one 128 x 240 x 32 product (two MMAs of K = 16):
 // N = 240 columns are 48 output blocks times the 5 limbs of a; the a operand
 // is stored once per tile as rows (J, i) = limb i of block J of a, reversed,
 // and the rows shift delta needs are the same rows moved by 5 per delta, so
@@ -115,11 +114,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
-// instruction descriptor: D f32, A and B bf16, both K-major, M = 128, N columns
-// (a multiple of 16, at most 256)
-__device__ __forceinline__ uint32_t idesc_n(uint32_t n) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((uint32_t)(MMA_M >> 4) << 24);
-}
+// instruction descriptor: D f32, A and B bf16, both K-major, N and M as given
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
+                           ((uint32_t)(MMA_M >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
     asm volatile(
@@ -424,23 +421,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                         const int nds = min(GROUP_D, tt.nd - gi * GROUP_D);
                         const int dg = tt.d_lo + gi * GROUP_D;
                         for (int s = 0; s < nds; ++s) {
-                            const int d = dg + s;
-                            // columns of the output blocks this shift meets (a block I0 + lb with
-                            // 0 <= I0 + lb - d < na), widened to multiples of 16; the tile's first
-                            // shift spans all 240 columns and clears the accumulator
-                            uint32_t c0 = 0, nc = MMA_N;
-                            if (gi != 0 || s != 0) {
-                                const int lb0 = max(0, d - tt.I0), lb1 = min(NBLK - 1, d + tt.na - 1 - tt.I0);
-                                c0 = (uint32_t)(NA_LIMB * lb0) & ~15u;
-                                nc = min((uint32_t)MMA_N, (uint32_t)(NA_LIMB * lb1 + NA_LIMB + 15) & ~15u) - c0;
-                            }
-                            const uint32_t idesc = idesc_n(nc);
-                            const uint32_t b_addr = sBa + (uint32_t)((NA_LIMB * (tt.d_hi - d) + (int)c0) * 16);
+                            // every shift spans all 240 columns (narrower MMAs for the blocks a
+                            // shift meets measured slower per product on this part)
+                            const uint32_t b_addr = sBa + (uint32_t)(NA_LIMB * (tt.d_hi - dg - s) * 16);
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 const uint64_t da = smem_desc(ha + (uint32_t)((4 * s + 2 * h) * 512), 512, 128);
                                 const uint64_t db = smem_desc(b_addr + 2 * h * B_LBO, B_LBO, 128);
-                                mma_bf16(tacc + c0, da, db, idesc, (gi == 0 && s == 0 && h == 0) ? 0u : 1u);
+                                mma_bf16(tacc, da, db, IDESC, (gi == 0 && s == 0 && h == 0) ? 0u : 1u);
                             }
                         }
                         mma_commit(bar(BAR_H_EMPTY + slot));

@@ -44,6 +44,25 @@ def test_ragged_small_batch(s):
     assert_equal(run_batch(packed, 4096, s=s), want, f"s={s}")
 
 
+@pytest.mark.parametrize("s", [1, 2, 4, 8, 16, 32])
+def test_ragged_small_batch_warp_form(s):
+    """Degrees below 4096: the warp-level form (one warp per range of positions)."""
+    da = np.array([0, 1, 5, 1000, 7, 0, 2047, 300, 64, 4095, 31, 33], np.int64)
+    db = np.array([0, 3, 5, 17, 2000, 999, 2047, 1, 64, 33, 4095, 32], np.int64)
+    packed = inputs.packed_batch(da, db, 78)
+    want = oracle.polymul_batch(*packed[:4], packed[4], P)
+    assert_equal(run_batch(packed, 4095, s=s), want, f"s={s}")
+
+
+@pytest.mark.parametrize("s", [4, 8])
+def test_warp_form_split_tiles(s):
+    """Few large pairs: every tile is cut across dozens of warps (partial-sum slots, counters)."""
+    packed = inputs.packed_batch(np.array([4000, 3999, 2500], np.int64), np.array([4000, 1, 4095], np.int64), 79)
+    want = oracle.polymul_batch(*packed[:4], packed[4], P)
+    for rep in range(2):  # the counters are back at zero for the second call
+        assert_equal(run_batch(packed, 4095, s=s), want, f"s={s} call {rep}")
+
+
 def test_batch_of_one_and_unsorted_path():
     packed = inputs.packed_batch(np.array([5000]), np.array([3000]), 5)
     assert_equal(run_batch(packed, 5000), oracle.polymul_batch(*packed[:4], packed[4], P))
