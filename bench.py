@@ -426,7 +426,15 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
     ms_g = median_ms(g.replay, 20, flush, stream)
     want = oracle.polymul_batch(a_data, a_off, b_data, b_off, c_off, P)
     assert np.array_equal(outb.cpu().numpy().view(np.uint32), want)
+    # the tensor-core form on the same batch (what PM_AUTO picks for degrees below 4096)
+    run_bt = lambda: pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_TENSOR, out=outb,
+                                total=outb.numel())
+    run_bt()
+    ms_bt = median_ms(run_bt, 10, flush, stream)
+    assert np.array_equal(outb.cpu().numpy().view(np.uint32), want)
     rows["batched_plain"] = {"workload": "4096 pairs, degrees log-uniform in [16,2048]", "s": s_b,
+                             "form": "warp-level units (degrees below 4096)",
+                             "tensor_form_ms_same_batch": ms_bt,
                              "macs": macs, "ms_graph": ms_g, "ms_direct": best[1],
                              "macs_per_s": macs / (ms_g * 1e-3), "products_per_s": 4096 / (ms_g * 1e-3),
                              "alu_frac": macs / (ms_g * 1e-3) / alu_peak_macs()}

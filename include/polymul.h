@@ -120,7 +120,8 @@ pm_status polymul_ntt(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64
                       uint32_t *c, uint32_t p, uint32_t g, void *stream);
 
 /*
- * polymul_batched - `batch` independent products in one persistent launch.
+ * polymul_batched - `batch` independent products, one stream-ordered sequence
+ * of launches (planning kernels, then one persistent product kernel).
  *
  *   a_data, a_off  CSR: pair i's a is a_data[a_off[i] .. a_off[i+1]), at least one word
  *   b_data, b_off  likewise for b
@@ -134,6 +135,11 @@ pm_status polymul_ntt(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64
  *   s              as for polymul_plain (PM_PLAIN / PM_AUTO); ignored by PM_TENSOR
  *   max_deg        an upper bound on every degree in the batch (the host cannot
  *                  read the device offsets); PM_TENSOR needs max_deg <= 4095
+ * PM_PLAIN is the s-blocked product of Section 5 with the positions of the
+ * whole batch shared out: when max_deg <= 4095 and s <= 32 each warp works on
+ * its own units (a small pair, or a piece of a large one), claimed from a
+ * counter; otherwise each persistent CTA takes an equal range of positions.
+ * The warp-level form holds up to 64 MiB of scratch per (device, stream).
  * PM_TENSOR computes the same residues on the tensor cores (bf16 limbs, fp32
  * accumulation that stays exact below 2^24); it needs p < 2^29 and
  * max_deg <= 4095, else returns PM_ERR_UNSUPPORTED.  PM_AUTO uses it when it
