@@ -184,42 +184,62 @@ __device__ __forceinline__ void compute_chunk(const uint32_t* sA, const uint32_t
 #pragma unroll
     for (int g = 0; g < NGW; ++g) load_group<S>(sA, base + g * KB, ring[(R - g) % R]);
     const uint32_t* bp = sB + r0;
-    for (int q0 = 0; q0 < nsub; q0 += R) {
+    // sub-step at ring position u (a constant once the loops below are unrolled,
+    // so the ring stays in fixed registers)
+    auto substep = [&](int u) {
+        load_group<S>(sA, base - KB, ring[(u + 1) % R]);  // group 0 of the next sub-step
+        uint32_t bv[KB];
+        if constexpr (KB >= 4) {
+#pragma unroll
+            for (int k4 = 0; k4 < KB; k4 += 4) {
+                const uint4 v = *reinterpret_cast<const uint4*>(bp + k4);
+                bv[k4] = v.x; bv[k4 + 1] = v.y; bv[k4 + 2] = v.z; bv[k4 + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < KB; ++k) bv[k] = bp[k];
+        }
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+#pragma unroll
+            for (int e = 0; e < S; ++e) {
+                const int t = e - k + KB - 1;  // window word of a[d - j]
+                acc[e] = mad_wide(ring[(u - t / KB + R) % R][t % KB], bv[k], acc[e]);
+            }
+        }
+        base -= KB;
+        bp += KB;
+    };
+    auto fold_all = [&]() {
+        fold_ctr = 0;
+        if (mp.fold_twice) {
+#pragma unroll
+            for (int e = 0; e < S; ++e) acc[e] = fold2(acc[e], mp.c32);
+        } else {
+#pragma unroll
+            for (int e = 0; e < S; ++e) acc[e] = fold_once(acc[e], mp.c32);
+        }
+    };
+    int q0 = 0;
+    if (mp.fold_every >= R) {
+        // whole blocks of R sub-steps, with no test inside: the fold falls due
+        // at most once per block and is done before the block if needed
+        for (; q0 + R <= nsub; q0 += R) {
+            if (fold_ctr + R > mp.fold_every) fold_all();
+#pragma unroll
+            for (int u = 0; u < R; ++u) substep(u);
+            fold_ctr += R;
+        }
+    }
+    // the last nsub mod R sub-steps (all of them when folds are due more often);
+    // at most fold_every sub-steps ever separate two folds
+    for (; q0 < nsub; q0 += R) {
 #pragma unroll
         for (int u = 0; u < R; ++u) {
             if (q0 + u < nsub) {
-                load_group<S>(sA, base - KB, ring[(u + 1) % R]);  // group 0 of the next sub-step
-                uint32_t bv[KB];
-                if constexpr (KB >= 4) {
-#pragma unroll
-                    for (int k4 = 0; k4 < KB; k4 += 4) {
-                        const uint4 v = *reinterpret_cast<const uint4*>(bp + k4);
-                        bv[k4] = v.x; bv[k4 + 1] = v.y; bv[k4 + 2] = v.z; bv[k4 + 3] = v.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < KB; ++k) bv[k] = bp[k];
-                }
-#pragma unroll
-                for (int k = 0; k < KB; ++k) {
-#pragma unroll
-                    for (int e = 0; e < S; ++e) {
-                        const int t = e - k + KB - 1;  // window word of a[d - j]
-                        acc[e] = mad_wide(ring[(u - t / KB + R) % R][t % KB], bv[k], acc[e]);
-                    }
-                }
-                if (++fold_ctr == mp.fold_every) {
-                    fold_ctr = 0;
-                    if (mp.fold_twice) {
-#pragma unroll
-                        for (int e = 0; e < S; ++e) acc[e] = fold2(acc[e], mp.c32);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < S; ++e) acc[e] = fold_once(acc[e], mp.c32);
-                    }
-                }
-                base -= KB;
-                bp += KB;
+                if (fold_ctr >= mp.fold_every) fold_all();
+                substep(u);
+                ++fold_ctr;
             }
         }
     }
