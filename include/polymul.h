@@ -143,7 +143,9 @@ pm_status polymul_ntt(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64
  * PM_TENSOR computes the same residues on the tensor cores (bf16 limbs, fp32
  * accumulation that stays exact below 2^24); it needs p < 2^29 and
  * max_deg <= 4095, else returns PM_ERR_UNSUPPORTED.  PM_AUTO uses it when it
- * applies.
+ * applies and max_deg > 2048 (below that the plain form measured faster).
+ * With s = 0 the plain form takes the tuned s of that size class (see
+ * polymul_tune_plain), else 8 from max_deg 1023 up, 4 from 63, else 2.
  * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_UNSUPPORTED, PM_ERR_NOMEM or PM_ERR_CUDA.
  */
 pm_status polymul_batched(int64_t batch, const uint32_t *a_data, const int64_t *a_off,

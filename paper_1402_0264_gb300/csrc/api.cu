@@ -212,12 +212,16 @@ pm_status polymul_batched(int64_t batch, const uint32_t* a_data, const int64_t* 
     pm_status rc = PM_OK;
     DeviceWorkspace* ws = workspace(stream, &rc);
     if (!ws) return rc;
-    if (mode == PM_TENSOR || (mode == PM_AUTO && tensor_ok)) {
+    // PM_AUTO: the tensor cores for batches with degrees above 2048; below, the
+    // warp-level plain form measured faster (4096 pairs of degrees in [16, 2048]:
+    // 0.19 ms against 0.21 ms)
+    const bool tensor_auto = tensor_ok && max_deg > 2048;
+    if (mode == PM_TENSOR || (mode == PM_AUTO && tensor_auto)) {
         rc = launch_batched_tensor(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg,
                                    (cudaStream_t)stream, ws);
         if (rc != PM_ERR_UNSUPPORTED || mode == PM_TENSOR) return rc;
     }
-    if (s == 0) s = default_s(max_deg + 1, max_deg + 1, p) > 4 ? 4 : default_s(max_deg + 1, max_deg + 1, p);
+    if (s == 0) s = default_s(max_deg + 1, max_deg + 1, p);
     return launch_batched_plain(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, s, max_deg,
                                 (cudaStream_t)stream, ws);
 }

@@ -48,6 +48,12 @@ constexpr int NTT_N2_LOG = 12;               // row length of the four-step layo
 constexpr int NTT_N2 = 1 << NTT_N2_LOG;
 constexpr int NTT_MAX_LOG = 24;              // N1 <= 4096 keeps a column block in shared memory
 constexpr int NTT_THREADS = 512;
+#ifndef NTT_ROW_MINB
+#define NTT_ROW_MINB 3   // row-pass CTAs per SM the compiler must fit (80 registers, no spills)
+#endif
+#ifndef NTT_COLS8_LOG
+#define NTT_COLS8_LOG 11 // column blocks of 8 (not 16) from this log2 N1 on: 64 KiB per CTA, 3 CTAs per SM
+#endif
 
 struct NttMod {
     uint32_t p;
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(NTT_THREADS) ntt_col_fwd_kernel(
 }
 
 // ---- four-step pass 2: per row, forward row transforms, product, inverse ----
-__global__ void __launch_bounds__(256) ntt_row_kernel(uint32_t* __restrict__ ta,
+__global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __restrict__ ta,
                                                       const uint32_t* __restrict__ tbuf,
                                                       int logn1, NttTables tb, NttMod md) {
     __shared__ uint32_t sA[ROW_WORDS];
@@ -560,7 +566,7 @@ pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m,
     if (rc != PM_OK) return rc;
     uint32_t* ta = reinterpret_cast<uint32_t*>(sc->ntt);
     uint32_t* tbuf = ta + N;
-    const int cols = logn1 >= 12 ? 8 : 16;  // a CTA's columns: cols * N1 words of shared memory
+    const int cols = logn1 >= NTT_COLS8_LOG ? 8 : 16;  // a CTA's columns: cols * N1 words of shared memory
     const size_t col_smem = sizeof(uint32_t) * (size_t)cols * ((size_t)1 << logn1);
     static int col_done[64] = {};
     if (!col_done[ws->device]) {

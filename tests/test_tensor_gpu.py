@@ -95,9 +95,11 @@ def test_matches_plain_batched_and_auto_mode():
     assert da.max() <= 2049
     t = run(packed, 2048, mode=pm.PM_TENSOR)
     pl = run(packed, 2048, mode=pm.PM_PLAIN)
-    au = run(packed, 2048, mode=pm.PM_AUTO)
+    au = run(packed, 2048, mode=pm.PM_AUTO)     # degrees up to 2048: the plain form
+    au4 = run(packed, 4095, mode=pm.PM_AUTO)    # a bound above 2048: the tensor form
     assert_equal(t, pl, "tensor vs plain")
     assert_equal(au, pl, "auto vs plain")
+    assert_equal(au4, pl, "auto (tensor) vs plain")
 
 
 def test_other_modulus():
