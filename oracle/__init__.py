@@ -8,6 +8,8 @@ CPU-baseline leg of ``bench.py`` may import this package.  The library in
   ``polymul_oracle.c`` (the long-multiplication definition of Section 5 of
   Haque, Moreno Maza, Xie, and a textbook radix-2 NTT used only as a faster
   exact evaluator).
+* ``divide``/``invmod``: Euclidean division a = q b + r over Z/pZ (Section 3),
+  one division step at a time from the top as in Algorithm 1.
 * ``model``: the printed cost formulas of Section 5 and the Graham-Brent bound
   of Section 2.4 (Theorem 1, Corollary 1), in fp64.
 """
@@ -68,6 +70,11 @@ def _load():
                                                      _u32p, _i64p, ctypes.c_uint32,
                                                      ctypes.c_uint32]
             lib.oracle_ntt_polymul_batch.restype = ctypes.c_int
+            lib.oracle_invmod.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+            lib.oracle_invmod.restype = ctypes.c_uint32
+            lib.oracle_divide.argtypes = [_u32p, ctypes.c_int64, _u32p, ctypes.c_int64, ctypes.c_uint32,
+                                          _u32p, _u32p]
+            lib.oracle_divide.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -143,3 +150,25 @@ def ntt_polymul_batch(a_data, a_off, b_data, b_off, c_off, p: int, g: int = 3) -
     if rc != 0:
         raise ValueError(f"oracle_ntt_polymul_batch failed ({rc})")
     return f
+
+
+def invmod(x: int, p: int) -> int:
+    """x^-1 mod p (0 when x has no inverse)."""
+    return int(_load().oracle_invmod(x, p))
+
+
+def divide(a, b, p: int):
+    """(q, r) with a = q b + r over Z/pZ and deg r < deg b (Section 3); len(a) >= len(b) >= 1,
+    b's leading coefficient invertible mod p.  q has len(a)-len(b)+1 words, r has len(b)-1."""
+    a, b = _u32(a), _u32(b)
+    q = np.zeros(len(a) - len(b) + 1 if len(a) >= len(b) else 0, dtype=np.uint32)
+    r = np.zeros(max(len(b) - 1, 0), dtype=np.uint32)
+    rc = _load().oracle_divide(_p(a, _u32p), len(a), _p(b, _u32p), len(b), p, _p(q, _u32p),
+                               _p(r, _u32p))
+    if rc == -1:
+        raise ValueError("oracle_divide: needs len(a) >= len(b) >= 1")
+    if rc == -2:
+        raise ValueError("oracle_divide: the leading coefficient of b has no inverse mod p")
+    if rc != 0:
+        raise MemoryError("oracle_divide")
+    return q, r

@@ -23,6 +23,12 @@
  *                             exact evaluator for sizes where the definition
  *                             is too slow, pinned against the definition
  *   oracle_powmod             modular exponentiation (square and multiply)
+ *   oracle_invmod             modular inverse (extended Euclidean algorithm)
+ *   oracle_divide             Euclidean division a = q b + r over Z/pZ
+ *                             (Section 3, "Polynomial division": the division
+ *                             steps of Algorithms 1-4, one leading
+ *                             coefficient cancelled per step, done here one
+ *                             step at a time)
  *
  * Plain C, single threaded, unoptimised on purpose.
  */
@@ -159,5 +165,48 @@ int oracle_ntt_polymul_batch(int64_t batch, const uint32_t *a, const int64_t *a_
         int rc = oracle_ntt_polymul(a + a_off[i], n, b + b_off[i], m, p, g, f + f_off[i]);
         if (rc != 0) return rc;
     }
+    return 0;
+}
+
+/* x^-1 mod p by the extended Euclidean algorithm; 0 when gcd(x, p) != 1. */
+uint32_t oracle_invmod(uint32_t x, uint32_t p) {
+    int64_t r0 = p, r1 = x % p, t0 = 0, t1 = 1;
+    while (r1 != 0) {
+        int64_t qt = r0 / r1, tmp;
+        tmp = r0 - qt * r1; r0 = r1; r1 = tmp;
+        tmp = t0 - qt * t1; t0 = t1; t1 = tmp;
+    }
+    if (r0 != 1) return 0;
+    if (t0 < 0) t0 += p;
+    return (uint32_t)t0;
+}
+
+/* Euclidean division over Z/pZ (Section 3): for a with n terms and b with m
+ * terms, n >= m >= 1, the unique q (n-m+1 terms) and r (the low m-1 terms)
+ * with a = q b + r and deg r < deg b.  The division steps run from the top,
+ * i = n-1 down to m-1, as in Algorithm 1: the current coefficient a[i] gives
+ * q[i-(m-1)] = a[i] lc(b)^-1, and that multiple of x^(i-(m-1)) b is
+ * subtracted from the remainder (which cancels a[i]).  lc(b) = b[m-1] must
+ * be invertible mod p.  Returns 0, -1 for bad sizes, -2 when b[m-1] has no
+ * inverse, -3 when out of memory. */
+int oracle_divide(const uint32_t *a, int64_t n, const uint32_t *b, int64_t m, uint32_t p,
+                  uint32_t *q, uint32_t *r) {
+    if (m < 1 || n < m) return -1;
+    uint32_t inv = oracle_invmod(b[m - 1] % p, p);
+    if (inv == 0) return -2;
+    uint32_t *rem = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)n);
+    if (!rem) return -3;
+    for (int64_t i = 0; i < n; ++i) rem[i] = a[i] % p;
+    for (int64_t i = n - 1; i >= m - 1; --i) {
+        uint32_t c = mulmod(rem[i], inv, p);
+        q[i - (m - 1)] = c;
+        for (int64_t j = 0; j < m; ++j) {
+            uint32_t t = mulmod(c, b[j] % p, p);
+            uint32_t *x = &rem[i - (m - 1) + j];
+            *x = *x >= t ? *x - t : *x + p - t;
+        }
+    }
+    for (int64_t i = 0; i < m - 1; ++i) r[i] = rem[i];
+    free(rem);
     return 0;
 }
