@@ -154,6 +154,32 @@ pm_status polymul_batched(int64_t batch, const uint32_t *a_data, const int64_t *
                           int mode, int s, int64_t max_deg, void *stream);
 
 /*
+ * polymul_divide - Euclidean division over Z/pZ (Section 3, "Polynomial
+ * division", Algorithms 3-4 with parameter s; s = 1 is the naive division of
+ * Algorithms 1-2): the unique q and r with a = q b + r and deg r < deg b.
+ *
+ *   a, deg_a   device array of deg_a+1 coefficients, deg_b <= deg_a <= PM_MAX_DEG
+ *   b, deg_b   device array of deg_b+1 coefficients; b[deg_b] must be invertible
+ *              mod p (nonzero when p is prime)
+ *   q          device array of deg_a-deg_b+1 words, written in full
+ *   r          device array of deg_b words (the remainder's deg_b low terms,
+ *              leading zeros kept); may be NULL when deg_b = 0
+ *   p          2 <= p < PM_MAX_P (need not be prime)
+ *   s          division steps per kernel launch, 1 <= s <= 256; 0 picks 256
+ *   stream     cudaStream_t as void*
+ * The steps run from the top coefficient down, s per launch (one launch per
+ * s quotient terms, after one set-up launch), so the call is stream-ordered
+ * and can be captured into a CUDA graph once its scratch (4 (deg_a + 1) + 256
+ * bytes per (device, stream)) exists.  A leading coefficient of b without an
+ * inverse sets PM_ERR_INVALID_ARG in the status word (polymul_sync_status);
+ * q and r are then undefined.
+ * Returns PM_OK, PM_ERR_INVALID_ARG (null pointer, degrees, s, overlapping
+ * arrays), PM_ERR_RANGE (p), PM_ERR_NOMEM or PM_ERR_CUDA.
+ */
+pm_status polymul_divide(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
+                         uint32_t *q, uint32_t *r, uint32_t p, int s, void *stream);
+
+/*
  * polymul_model_predict - the cost model of the s-blocked product
  * (Section 5 printed formulas; Theorem 1 and Corollary 1 of Section 2.4).
  * Host-only; no GPU needed.

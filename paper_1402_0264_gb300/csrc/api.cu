@@ -195,6 +195,24 @@ pm_status polymul_ntt(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64
     return launch_ntt(a, deg_a + 1, b, deg_b + 1, c, p, g, (cudaStream_t)stream, ws);
 }
 
+pm_status polymul_divide(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64_t deg_b, uint32_t* q,
+                         uint32_t* r, uint32_t p, int s, void* stream) {
+    if (!a || !b || !q || (deg_b > 0 && !r)) return PM_ERR_INVALID_ARG;
+    if (deg_b < 0 || deg_a < deg_b || deg_a > PM_MAX_DEG) return PM_ERR_INVALID_ARG;
+    if (p < 2 || p >= PM_MAX_P) return PM_ERR_RANGE;
+    if (s < 0 || s > 256) return PM_ERR_INVALID_ARG;
+    const int64_t nq = deg_a - deg_b + 1;
+    if (overlaps(q, nq, a, deg_a + 1) || overlaps(q, nq, b, deg_b + 1)) return PM_ERR_INVALID_ARG;
+    if (deg_b > 0 && (overlaps(r, deg_b, a, deg_a + 1) || overlaps(r, deg_b, b, deg_b + 1) ||
+                      overlaps(r, deg_b, q, nq)))
+        return PM_ERR_INVALID_ARG;
+    if (s == 0) s = 256;
+    pm_status rc = PM_OK;
+    DeviceWorkspace* ws = workspace(stream, &rc);
+    if (!ws) return rc;
+    return launch_divide(a, deg_a + 1, b, deg_b + 1, q, r, p, s, (cudaStream_t)stream, ws);
+}
+
 pm_status polymul_batched(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                           const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                           const int64_t* c_off, uint32_t p, int mode, int s, int64_t max_deg,
@@ -325,6 +343,7 @@ pm_status polymul_release(void) {
             if (sc->plan) cudaFree(sc->plan);
             if (sc->tc) cudaFree(sc->tc);
             if (sc->ntt) cudaFree(sc->ntt);
+            if (sc->div) cudaFree(sc->div);
             delete sc;
         }
         delete mp;

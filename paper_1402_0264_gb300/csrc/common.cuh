@@ -83,6 +83,8 @@ struct StreamScratch {
     size_t tc_bytes = 0;
     void* ntt = nullptr;           // transform buffers
     size_t ntt_bytes = 0;
+    void* div = nullptr;           // division: working copy of the dividend, inverse of lc(b)
+    size_t div_bytes = 0;
 };
 
 // Per-device state owned by the library.
@@ -125,5 +127,7 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
                                 const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                 const int64_t* c_off, uint32_t p, int64_t max_deg,
                                 cudaStream_t st, DeviceWorkspace* ws);
+pm_status launch_divide(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* q, uint32_t* r,
+                        uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws);
 
 }  // namespace pm

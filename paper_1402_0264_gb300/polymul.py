@@ -43,6 +43,7 @@ def _declare(lib):
         "polymul_ntt": ([V, I64, V, I64, V, U32, U32, V], INT),
         "polymul_plain_noalloc": ([V, I64, V, I64, V, U32, INT, V], INT),
         "polymul_batched": ([I64, V, V, V, V, V, V, U32, INT, INT, I64, V], INT),
+        "polymul_divide": ([V, I64, V, I64, V, V, U32, INT, V], INT),
         "polymul_model_predict": ([I64, I64, INT, INT, D, D, ctypes.POINTER(D)], INT),
         "polymul_tune_plain": ([V, I64, V, I64, V, U32, INT, V, ctypes.POINTER(INT),
                                 ctypes.POINTER(ctypes.c_float)], INT),
@@ -156,6 +157,21 @@ def batched(a_data, a_off, b_data, b_off, c_off, max_deg: int, p: int = P_DEFAUL
                                  _dev_words(out, "out"), _dev_i64(c_off, "c_off"), p, mode, s,
                                  max_deg, _stream_ptr(stream)), "polymul_batched")
     return out
+
+
+def divide(a, b, p: int = P_DEFAULT, s: int = 0, q=None, r=None, stream=None):
+    """(q, r) with a = q b + r over Z/pZ, deg r < deg b (Section 3); s division steps per launch."""
+    nq = a.numel() - b.numel() + 1
+    if nq < 1:
+        raise ValueError("divide needs len(a) >= len(b)")
+    q = _alloc(nq, a) if q is None else q
+    r = _alloc(b.numel() - 1, a) if r is None else r
+    if q.numel() != nq or r.numel() != b.numel() - 1:
+        raise ValueError("q must hold len(a) - len(b) + 1 words and r len(b) - 1")
+    rp = _dev_words(r, "r") if r.numel() > 0 else ctypes.c_void_p(None)
+    _check(lib().polymul_divide(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"), b.numel() - 1,
+                                _dev_words(q, "q"), rp, p, s, _stream_ptr(stream)), "polymul_divide")
+    return q, r
 
 
 def model_predict(n: int, m: int, s: int, ell: int, U: float, P: float) -> dict:

@@ -96,3 +96,19 @@ def test_model_rejects_bad_args(lib):
         pm.model_predict(100, 4, 8, 256, 10.0, 152.0)   # s > m
     with pytest.raises(pm.PolymulError):
         pm.model_predict(100, 100, 4, 256, 0.0, 152.0)  # U <= 0
+
+
+def test_divide_validation_happens_on_host(lib):
+    f = lib.polymul_divide
+    Q = ctypes.c_void_p(0x30000000)
+    R = ctypes.c_void_p(0x40000000)
+    P = pm.P_DEFAULT
+    assert f(NULL, 5, FAKE2, 3, Q, R, P, 0, NULL) == 1          # null dividend
+    assert f(FAKE, 5, FAKE2, 3, Q, NULL, P, 0, NULL) == 1       # null remainder with deg b > 0
+    assert f(FAKE, 2, FAKE2, 3, Q, R, P, 0, NULL) == 1          # deg a < deg b
+    assert f(FAKE, 5, FAKE2, -1, Q, R, P, 0, NULL) == 1         # negative degree
+    assert f(FAKE, 5, FAKE2, 3, Q, R, 1, 0, NULL) == 2          # p < 2
+    assert f(FAKE, 5, FAKE2, 3, Q, R, P, 257, NULL) == 1        # s too large
+    assert f(FAKE, 5, FAKE2, 3, Q, R, P, -1, NULL) == 1         # negative s
+    assert f(FAKE, 5, FAKE2, 3, FAKE, R, P, 0, NULL) == 1       # q overlapping a
+    assert f(FAKE, 5, FAKE2, 3, Q, Q, P, 0, NULL) == 1          # r overlapping q
