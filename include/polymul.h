@@ -165,7 +165,7 @@ pm_status polymul_batched(int64_t batch, const uint32_t *a_data, const int64_t *
  *   r          device array of deg_b words (the remainder's deg_b low terms,
  *              leading zeros kept); may be NULL when deg_b = 0
  *   p          2 <= p < PM_MAX_P (need not be prime)
- *   s          division steps per kernel launch, 1 <= s <= 256; 0 picks 256
+ *   s          division steps per kernel launch, 1 <= s <= 256; 0 picks 128
  *   stream     cudaStream_t as void*
  * The steps run from the top coefficient down, s per launch (one launch per
  * s quotient terms, after one set-up launch), so the call is stream-ordered

@@ -206,7 +206,7 @@ pm_status polymul_divide(const uint32_t* a, int64_t deg_a, const uint32_t* b, in
     if (deg_b > 0 && (overlaps(r, deg_b, a, deg_a + 1) || overlaps(r, deg_b, b, deg_b + 1) ||
                       overlaps(r, deg_b, q, nq)))
         return PM_ERR_INVALID_ARG;
-    if (s == 0) s = 256;
+    if (s == 0) s = 128;  // the fastest measured on GB300 (degree 32767 by 16383)
     pm_status rc = PM_OK;
     DeviceWorkspace* ws = workspace(stream, &rc);
     if (!ws) return rc;

@@ -10,9 +10,11 @@
 // own stretch of the remainder below the head, redundantly with the other
 // blocks for the head.  Here each launch of div_round_kernel is one such
 // call, with the same split of the work:
-//   head: one warp runs the round's division steps on the s-head in shared
-//         memory (step k: q_k = head[k] lc(b)^-1, then head[t] -= q_k b[d_b - (t - k)]
-//         for t > k), and keeps the s quotient coefficients;
+//   head: one warp runs the round's division steps on the s-head (step k:
+//         q_k = head[k] lc(b)^-1, then head[t] -= q_k b[d_b - (t - k)] for
+//         t > k), 32 steps at a time with the group's entries in registers and
+//         the later entries updated once per group, and keeps the s quotient
+//         coefficients;
 //   body: every other thread then applies all s steps to its positions at
 //         once, r[x] -= sum_k q_k b[x - (i - k) + d_b], as a short convolution
 //         summed lazily in 64 bits and reduced once per 8 terms (the same
@@ -26,8 +28,14 @@
 
 namespace pm {
 
-constexpr int DIV_THREADS = 256;
-constexpr int DIV_E = 2;                         // remainder positions per thread in the body
+#ifndef PM_DIV_THREADS
+#define PM_DIV_THREADS 128   // measured: 128-thread blocks, one body position per thread
+#endif
+#ifndef PM_DIV_E
+#define PM_DIV_E 1
+#endif
+constexpr int DIV_THREADS = PM_DIV_THREADS;
+constexpr int DIV_E = PM_DIV_E;                  // remainder positions per thread in the body
 constexpr int DIV_BODY = DIV_THREADS * DIV_E;    // positions below the head per block
 constexpr int DIV_SMAX = 256;                    // largest s
 
@@ -83,6 +91,7 @@ __global__ void __launch_bounds__(DIV_THREADS) div_round_kernel(uint32_t* __rest
                                                                 uint64_t mu) {
     __shared__ uint32_t head[DIV_SMAX];          // coefficients i - t of the remainder
     __shared__ uint32_t bh[DIV_SMAX];            // b[d_b - t]
+    __shared__ uint32_t bhq[DIV_SMAX];           // its Shoup quotients floor(bh 2^32 / p)
     __shared__ uint32_t sq[DIV_SMAX];            // the round's quotient coefficients
     __shared__ uint32_t sb[DIV_BODY + DIV_SMAX]; // b window of the body
     const uint32_t w = inv[0], wq = inv[1];
@@ -95,7 +104,9 @@ __global__ void __launch_bounds__(DIV_THREADS) div_round_kernel(uint32_t* __rest
     const int64_t bx0 = top - i + d_b - (DIV_BODY - 1);
     for (int t = tid; t < s; t += DIV_THREADS) {
         head[t] = i - t >= 0 ? work[i - t] : 0u;
-        bh[t] = d_b - t >= 0 ? b[d_b - t] : 0u;
+        const uint32_t bv = d_b - t >= 0 ? b[d_b - t] : 0u;
+        bh[t] = bv;
+        bhq[t] = (uint32_t)(((uint64_t)bv << 32) / p);
     }
     for (int v = tid; v < DIV_BODY + s - 1; v += DIV_THREADS) {
         const int64_t bi = bx0 + v;
@@ -103,11 +114,26 @@ __global__ void __launch_bounds__(DIV_THREADS) div_round_kernel(uint32_t* __rest
     }
     __syncthreads();
     if (tid < 32) {  // the head: one warp, the steps in order
-        for (int k = 0; k < ks; ++k) {
-            const uint32_t qk = div_mul_const(head[k], w, wq, p);
-            if (tid == 0) sq[k] = qk;
-            for (int t = k + 1 + tid; t < s; t += 32)
-                head[t] = div_sub(head[t], barrett((uint64_t)qk * bh[t - k], p, mu), p);
+        // Steps in groups of 32: lane j holds head entry k0 + j of the group in a
+        // register, so a step costs one shuffle and one product per lane on the
+        // sequential path; the group's 32 quotient terms then update the entries
+        // beyond the group at once.
+        for (int k0 = 0; k0 < ks; k0 += 32) {
+            const int kend = min(k0 + 32, ks);
+            const int t = k0 + tid;
+            uint32_t h = t < s ? head[t] : 0u;
+            for (int k = k0; k < kend; ++k) {
+                const uint32_t qk = div_mul_const(__shfl_sync(0xffffffffu, h, k - k0), w, wq, p);
+                if (tid == 0) sq[k] = qk;
+                if (t > k && t < s) h = div_sub(h, div_mul_const(qk, bh[t - k], bhq[t - k], p), p);
+            }
+            if (t < s) head[t] = h;
+            __syncwarp();
+            for (int u = k0 + 32 + tid; u < s; u += 32) {  // entries after the group's 32
+                uint64_t acc = 0;  // at most 32 reduced products: below 2^35
+                for (int k = k0; k < kend; ++k) acc += div_mul_const(sq[k], bh[u - k], bhq[u - k], p);
+                head[u] = div_sub(head[u], barrett(acc, p, mu), p);
+            }
             __syncwarp();
         }
     }
