@@ -123,9 +123,13 @@ __global__ void __launch_bounds__(DIV_THREADS) div_round_kernel(uint32_t* __rest
             const int t = k0 + tid;
             uint32_t h = t < s ? head[t] : 0u;
             for (int k = k0; k < kend; ++k) {
+                // branch-free: every lane stores the same q_k, and the update is a select
                 const uint32_t qk = div_mul_const(__shfl_sync(0xffffffffu, h, k - k0), w, wq, p);
-                if (tid == 0) sq[k] = qk;
-                if (t > k && t < s) h = div_sub(h, div_mul_const(qk, bh[t - k], bhq[t - k], p), p);
+                sq[k] = qk;
+                const bool live = t > k && t < s;
+                const int j = live ? t - k : 0;
+                const uint32_t upd = div_sub(h, div_mul_const(qk, bh[j], bhq[j], p), p);
+                h = live ? upd : h;
             }
             if (t < s) head[t] = h;
             __syncwarp();
