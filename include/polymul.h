@@ -77,6 +77,20 @@ pm_status polymul_plain(const uint32_t *a, int64_t deg_a, const uint32_t *b, int
                         uint32_t *c, uint32_t p, int s, void *stream);
 
 /*
+ * polymul_plain_ell - polymul_plain with a chosen number of threads per
+ * block, the paper's l (Section 5: l threads per thread-block, each forming
+ * s outputs; with s and U it fixes the model's N_s, L_s, C_s).  For the
+ * study of the model's predictions over (s, l); the result is the same.
+ *
+ *   ell        128, 256 (polymul_plain's block) or 512
+ *   s          1, 2, 4, 8, 16, 32 or 64 (no tuned default)
+ *   other arguments as for polymul_plain.
+ * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_RANGE or PM_ERR_CUDA.
+ */
+pm_status polymul_plain_ell(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
+                            uint32_t *c, uint32_t p, int s, int ell, void *stream);
+
+/*
  * polymul_plain_noalloc - polymul_plain for callers that cannot allocate.
  * The paper has no counterpart: this is a deployment variant of the same
  * product.  Some callers cannot let a library call cudaMalloc: code that runs

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpolymul.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "plain.cu", "ntt.cu", "tensor.cu", "div.cu"]
+SOURCES = ["api.cu", "plain.cu", "plain_ell.cu", "ntt.cu", "tensor.cu", "div.cu"]
+DEPS = {"plain_ell.cu": ["plain.cu"]}  # sources that include another source
 
 
 def _nvcc() -> str:
@@ -49,7 +50,8 @@ def build(force: bool = False, ptxas_info: bool = False, verbose: bool = False) 
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
-        if force or ptxas_info or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr):
+        newest = max([os.path.getmtime(s), hdr] + [os.path.getmtime(os.path.join(CSRC, d)) for d in DEPS.get(src, [])])
+        if force or ptxas_info or not os.path.exists(o) or os.path.getmtime(o) < newest:
             jobs.append((s, o))
 
     def compile_one(job):

@@ -186,6 +186,17 @@ pm_status polymul_plain(const uint32_t* a, int64_t deg_a, const uint32_t* b, int
     return launch_plain(a, deg_a + 1, b, deg_b + 1, c, p, s, (cudaStream_t)stream, ws);
 }
 
+pm_status polymul_plain_ell(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64_t deg_b, uint32_t* c,
+                            uint32_t p, int s, int ell, void* stream) {
+    pm_status rc = check_pair(a, deg_a, b, deg_b, c, p);
+    if (rc != PM_OK) return rc;
+    if (!valid_s(s)) return PM_ERR_INVALID_ARG;
+    if (ell != 128 && ell != 256 && ell != 512) return PM_ERR_INVALID_ARG;
+    DeviceWorkspace* ws = workspace(stream, &rc);
+    if (!ws) return rc;
+    return launch_plain_ell(a, deg_a + 1, b, deg_b + 1, c, p, s, ell, (cudaStream_t)stream, ws);
+}
+
 pm_status polymul_ntt(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64_t deg_b,
                       uint32_t* c, uint32_t p, uint32_t g, void* stream) {
     pm_status rc = check_pair(a, deg_a, b, deg_b, c, p);

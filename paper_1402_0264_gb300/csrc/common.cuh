@@ -127,6 +127,8 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
                                 const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                 const int64_t* c_off, uint32_t p, int64_t max_deg,
                                 cudaStream_t st, DeviceWorkspace* ws);
+pm_status launch_plain_ell(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c, uint32_t p,
+                           int s, int ell, cudaStream_t st, DeviceWorkspace* ws);
 pm_status launch_divide(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* q, uint32_t* r,
                         uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws);
 

@@ -54,12 +54,14 @@ constexpr int FIRST_CHUNK = 512; // a CTA's very first chunk: short, so that its
 #define PM_MINB 0                // __launch_bounds__ minimum blocks per SM (0: none)
 #endif
 #if PM_MINB > 0
-#define PM_BOUNDS __launch_bounds__(32 * PM_WB, PM_MINB)
+#define PM_BOUNDS(W) __launch_bounds__(32 * (W), PM_MINB)
 #else
-#define PM_BOUNDS __launch_bounds__(32 * PM_WB)
+#define PM_BOUNDS(W) __launch_bounds__(32 * (W))
 #endif
 
-template <int S>
+// W = warps per CTA (the paper's l = 32 W threads per block); WB by default,
+// 4 and 16 for the block-size study (polymul_plain_ell).
+template <int S, int W = WB>
 struct Cfg {
     static constexpr int KB = S < 8 ? S : 8;                   // b coefficients per sub-step
     static constexpr int NGW = (S + KB - 1 + KB - 1) / KB;     // window groups of KB words
@@ -70,7 +72,7 @@ struct Cfg {
     static constexpr int A_WORDS = 4 * (A_CHUNKS + A_CHUNKS / 8 + 2);
     static constexpr int PSTRIDE = TD + 32;                    // row of per-warp partial sums
     static constexpr int BUF_WORDS = A_WORDS + CHUNK_MAX;       // one staging buffer
-    static constexpr size_t SMEM = 4 * (size_t)(2 * BUF_WORDS + WB * PSTRIDE + TD);
+    static constexpr size_t SMEM = 4 * (size_t)(2 * BUF_WORDS + W * PSTRIDE + TD);
 };
 
 // word offset of logical a-window word i (16-byte chunks, a pad chunk every 8)
@@ -82,13 +84,13 @@ struct Smem {
     uint32_t* red;
 };
 
-template <int S>
+template <int S, int W = WB>
 __device__ __forceinline__ Smem carve(uint32_t* base) {
-    using C = Cfg<S>;
+    using C = Cfg<S, W>;
     Smem s;
     s.buf = base;
     s.part = s.buf + 2 * C::BUF_WORDS;
-    s.red = s.part + WB * C::PSTRIDE;
+    s.red = s.part + W * C::PSTRIDE;
     return s;
 }
 
@@ -247,20 +249,20 @@ __device__ __forceinline__ void compute_chunk(const uint32_t* sA, const uint32_t
 
 // Addition phase inside the CTA: every warp reduces its sums mod p, then the
 // 8 partial sums of each output are added.  Leaves red[o] in [0, p).
-template <int S>
+template <int S, int W = WB>
 __device__ __forceinline__ void cta_reduce(uint64_t (&acc)[S], const ModParams& mp,
                                            const Smem& sm) {
-    using C = Cfg<S>;
+    using C = Cfg<S, W>;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
 #pragma unroll
     for (int e = 0; e < S; ++e)
         sm.part[warp * C::PSTRIDE + (S + 1) * lane + e] = barrett(fold2(acc[e], mp.c32), mp.p, mp.mu);
     __syncthreads();
-    for (int o = threadIdx.x; o < C::TD; o += NT) {
+    for (int o = threadIdx.x; o < C::TD; o += 32 * W) {
         uint64_t s = 0;
 #pragma unroll
-        for (int w = 0; w < WB; ++w) s += sm.part[w * C::PSTRIDE + o + o / S];
+        for (int w = 0; w < W; ++w) s += sm.part[w * C::PSTRIDE + o + o / S];
         sm.red[o] = barrett(s, mp.p, mp.mu);
     }
     __syncthreads();
@@ -379,22 +381,23 @@ __device__ __forceinline__ Seg make_seg(int64_t x, int64_t x1, int& pi, int64_t&
 // Addition phase of a finished segment: the CTA's sums, then either the
 // tile's outputs (the CTA owns the whole tile) or a partial-sum slot; the CTA
 // that brings the tile's counter to its last value adds the slots and writes.
-template <int S>
+template <int S, int W = WB>
 __device__ __forceinline__ void finish_segment(const Seg& sg, uint64_t (&acc)[S], const ModParams& mp,
                                                const Smem& sm, const Split& sp, int64_t k, int64_t x0,
                                                SkScratch sk, int* s_last) {
-    using C = Cfg<S>;
-    cta_reduce<S>(acc, mp, sm);
+    using C = Cfg<S, W>;
+    constexpr int NTW = 32 * W;
+    cta_reduce<S, W>(acc, mp, sm);
     const int L = sg.n + sg.m - 1;
     if (sg.x == sg.s_tile && sg.x_end == sg.e_tile) {
-        for (int o = threadIdx.x; o < C::TD; o += NT)
+        for (int o = threadIdx.x; o < C::TD; o += NTW)
             if (sg.d0 + o < L) sg.c[sg.d0 + o] = sm.red[o];
         return;
     }
     const int64_t k1 = sp.owner(sg.s_tile), k2 = sp.owner(sg.e_tile - 1);
     const int64_t slot = 2 * k + (sg.x == x0 ? 0 : 1);
     uint32_t* mine = sk.slots + slot * C::TD;
-    for (int o = threadIdx.x; o < C::TD; o += NT) mine[o] = sm.red[o];
+    for (int o = threadIdx.x; o < C::TD; o += NTW) mine[o] = sm.red[o];
     __syncthreads();
     if (threadIdx.x == 0) {
         // the barrier orders every thread's slot writes before this fence, and a
@@ -409,7 +412,7 @@ __device__ __forceinline__ void finish_segment(const Seg& sg, uint64_t (&acc)[S]
     __syncthreads();
     if (*s_last) {  // every other contributor has written its slot
         const int64_t first_slot = 2 * k1 + (sp.start(k1) == sg.s_tile ? 0 : 1);
-        for (int o = threadIdx.x; o < C::TD; o += NT) {
+        for (int o = threadIdx.x; o < C::TD; o += NTW) {
             // four independent sums keep several L2 reads in flight
             uint64_t s0 = __ldcg(sk.slots + first_slot * C::TD + o), s1 = 0, s2 = 0, s3 = 0;
             int64_t kk = k1 + 1;
@@ -431,17 +434,18 @@ __device__ __forceinline__ void finish_segment(const Seg& sg, uint64_t (&acc)[S]
 // BATCH = true: pair i from the CSR arrays; prefix[i] = positions before pair i.
 // The CTA's chunks form one stream across its segments: the next chunk (of
 // this segment or the next) is copied in while the current one is used.
-template <int S, bool BATCH>
-__global__ void PM_BOUNDS plain_sk_kernel(
+template <int S, bool BATCH, int W = WB>
+__global__ void PM_BOUNDS(W) plain_sk_kernel(
     const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
     const uint32_t* __restrict__ b_data, const int64_t* __restrict__ b_off,
     uint32_t* __restrict__ c_data, const int64_t* __restrict__ c_off, int n1, int m1,
     const int64_t* __restrict__ prefix, int batch, ModParams mp, SkScratch sk) {
-    using C = Cfg<S>;
+    using C = Cfg<S, W>;
+    constexpr int NTW = 32 * W;
     constexpr int KB = C::KB;
     extern __shared__ uint4 smem_raw[];
     __shared__ int s_last;
-    const Smem sm = carve<S>(reinterpret_cast<uint32_t*>(smem_raw));
+    const Smem sm = carve<S, W>(reinterpret_cast<uint32_t*>(smem_raw));
     int64_t G;
     if constexpr (BATCH) {
         G = prefix[batch];
@@ -475,7 +479,7 @@ __global__ void PM_BOUNDS plain_sk_kernel(
         cur.nchunks = 1 + (cur.jb1 - cur.jb0 - FIRST_CHUNK + CHUNK_MAX - 1) / CHUNK_MAX;
     }
     stage_chunk<S, C::A_WORDS>(cur.a, cur.n, cur.b, cur.d0, chunk_dims<KB>(cur.jb0, cur.jb1, 0, cur.f), sm.buf,
-                               threadIdx.x, NT);
+                               threadIdx.x, NTW);
     for (;;) {
         Seg nxt = cur;
         int nci = ci + 1;
@@ -491,7 +495,7 @@ __global__ void PM_BOUNDS plain_sk_kernel(
         }
         if (has_next) {  // the next chunk streams in while this one is used
             stage_chunk<S, C::A_WORDS>(nxt.a, nxt.n, nxt.b, nxt.d0, chunk_dims<KB>(nxt.jb0, nxt.jb1, nci, nxt.f),
-                                       sm.buf + (bi ^ 1) * C::BUF_WORDS, threadIdx.x, NT);
+                                       sm.buf + (bi ^ 1) * C::BUF_WORDS, threadIdx.x, NTW);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -504,9 +508,9 @@ __global__ void PM_BOUNDS plain_sk_kernel(
         }
         const uint32_t* sA = sm.buf + bi * C::BUF_WORDS;
         compute_chunk<S>(sA, sA + C::A_WORDS, chunk_dims<KB>(cur.jb0, cur.jb1, ci, cur.f).CL, mp, acc, fold_ctr,
-                         threadIdx.x >> 5, WB);
+                         threadIdx.x >> 5, W);
         __syncthreads();  // this buffer is refilled by the next staging
-        if (ci == cur.nchunks - 1) finish_segment<S>(cur, acc, mp, sm, sp, k, x0, sk, &s_last);
+        if (ci == cur.nchunks - 1) finish_segment<S, W>(cur, acc, mp, sm, sp, k, x0, sk, &s_last);
         if (!has_next) break;
         cur = nxt;
         ci = nci;
@@ -752,6 +756,7 @@ __device__ __forceinline__ int64_t pair_positions(int64_t n, int64_t m, int64_t 
     return cum_len(n, m, td, ntiles_of(n, m, td));
 }
 
+#ifndef PM_PLAIN_STUDY_TU
 __global__ void __launch_bounds__(PLAN_THREADS) batch_plan_kernel(
     int batch, const int64_t* __restrict__ a_off, const int64_t* __restrict__ b_off,
     const int64_t* __restrict__ c_off, int64_t max_deg, int td, int64_t* prefix, int* status) {
@@ -790,6 +795,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) batch_plan_kernel(
     }
     if (tid == PLAN_THREADS - 1) prefix[batch] = s_scan[PLAN_THREADS - 1];
 }
+#endif  // PM_PLAIN_STUDY_TU
 
 // inclusive scan of one value per thread over the block
 __device__ __forceinline__ long long block_scan(long long v, long long* sh) {
@@ -815,6 +821,7 @@ __device__ __forceinline__ long long block_scan(long long v, long long* sh) {
 // in the claim order (rank) and the three tiers' sizes.  warp_fill_kernel (one
 // warp per pair): the table of the pair of every unit; it also resets the
 // claim counter.
+#ifndef PM_PLAIN_STUDY_TU
 __global__ void __launch_bounds__(256) warp_count_kernel(int batch, const int64_t* __restrict__ a_off,
                                                          const int64_t* __restrict__ b_off,
                                                          const int64_t* __restrict__ c_off, int64_t max_deg, int td,
@@ -838,6 +845,7 @@ __global__ void __launch_bounds__(256) warp_count_kernel(int batch, const int64_
         bsum[blockIdx.x] = t;
     }
 }
+#endif  // PM_PLAIN_STUDY_TU
 
 __device__ __forceinline__ int64_t div_up(int64_t x, int64_t q) {
     return (x < 0x7fffffff && q < 0x7fffffff) ? (int64_t)(((uint32_t)x + (uint32_t)q - 1) / (uint32_t)q)
@@ -873,6 +881,7 @@ __device__ __forceinline__ void block_scan3(long long& x0, long long& x1, long l
     __syncthreads();  // sh is free again
 }
 
+#ifndef PM_PLAIN_STUDY_TU
 __global__ void __launch_bounds__(PLAN_THREADS) warp_plan_kernel(int batch, int td, WkPlan pl, int* status) {
     // pairs in rounds of PLAN_THREADS, pair r PLAN_THREADS + tid by thread tid
     __shared__ long long s_scan[96];
@@ -936,8 +945,10 @@ __global__ void __launch_bounds__(PLAN_THREADS) warp_plan_kernel(int batch, int 
         pl.sched[3] = bad ? 0 : b2;
     }
 }
+#endif  // PM_PLAIN_STUDY_TU
 
 // The unit table (claim order: pieces, tier 1, tier 2), one warp per pair.
+#ifndef PM_PLAIN_STUDY_TU
 __global__ void __launch_bounds__(256) warp_fill_kernel(int batch, WkPlan pl) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -958,6 +969,7 @@ __global__ void __launch_bounds__(256) warp_fill_kernel(int batch, WkPlan pl) {
     const int64_t k0 = pl.kbase[i], k1 = pl.kbase[i + 1];
     for (int64_t k = k0 + lane; k < k1; k += 32) pl.unit_pair[k] = i;
 }
+#endif  // PM_PLAIN_STUDY_TU
 
 // ---------------------------------------------------------------------------
 // Host launchers.
@@ -1007,14 +1019,14 @@ static SkScratch sk_carve(void* base) {
     return s;
 }
 
-template <int S>
+template <int S, int W = WB>
 static pm_status launch_pair_s(const uint32_t* a, int n, const uint32_t* b, int m, uint32_t* c,
                                uint32_t p, cudaStream_t st, DeviceWorkspace* ws) {
-    using C = Cfg<S>;
-    auto kern = plain_sk_kernel<S, false>;
+    using C = Cfg<S, W>;
+    auto kern = plain_sk_kernel<S, false, W>;
     static int occ_cache[64] = {};
     int occ = 0;
-    cudaError_t e = kernel_setup(kern, C::SMEM, ws->device, occ_cache, &occ);
+    cudaError_t e = kernel_setup(kern, C::SMEM, ws->device, occ_cache, &occ, 32 * W);
     if (e != cudaSuccess) return cuda_fail(e);
     const int64_t nn = std::max(n, m), mm = std::min(n, m);
     const int64_t G = cum_len(nn, mm, C::TD, ntiles_of(nn, mm, C::TD));
@@ -1026,7 +1038,7 @@ static pm_status launch_pair_s(const uint32_t* a, int n, const uint32_t* b, int 
     rc = ensure_scratch(&sc->sk, &sc->sk_bytes, sk_bytes(P, C::TD), st, /*zero=*/true);
     if (rc != PM_OK) return rc;
     const ModParams mp = host_mod_params(p, C::KB);
-    kern<<<(unsigned)P, NT, C::SMEM, st>>>(a, nullptr, b, nullptr, c, nullptr, n, m, nullptr, 0, mp,
+    kern<<<(unsigned)P, 32 * W, C::SMEM, st>>>(a, nullptr, b, nullptr, c, nullptr, n, m, nullptr, 0, mp,
                                            sk_carve(sc->sk));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
@@ -1034,6 +1046,7 @@ static pm_status launch_pair_s(const uint32_t* a, int n, const uint32_t* b, int 
     return PM_OK;
 }
 
+#ifndef PM_PLAIN_STUDY_TU
 pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c,
                        uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws) {
     const int ni = (int)n, mi = (int)m;
@@ -1048,7 +1061,9 @@ pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t 
         default: return PM_ERR_INVALID_ARG;
     }
 }
+#endif  // PM_PLAIN_STUDY_TU
 
+#ifndef PM_PLAIN_STUDY_TU
 // Warp-level form of the batched product (degrees below WK_MAX_DEG).
 template <int S>
 static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
@@ -1097,6 +1112,7 @@ static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, co
     return PM_OK;
 }
 
+
 template <int S>
 static pm_status launch_batched_s(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                   const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
@@ -1132,6 +1148,8 @@ static pm_status launch_batched_s(int64_t batch, const uint32_t* a_data, const i
     return PM_OK;
 }
 
+#endif  // PM_PLAIN_STUDY_TU
+#ifndef PM_PLAIN_STUDY_TU
 pm_status launch_batched_plain(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                const int64_t* c_off, uint32_t p, int s, int64_t max_deg,
@@ -1145,9 +1163,36 @@ pm_status launch_batched_plain(int64_t batch, const uint32_t* a_data, const int6
         default: return PM_ERR_INVALID_ARG;
     }
 }
+#endif  // PM_PLAIN_STUDY_TU
+
+#ifdef PM_PLAIN_STUDY_TU
+// The block-size study: the same product with l = 128, 256 or 512 threads per
+// CTA (4, 8 or 16 warps; the paper's l of Section 5).
+pm_status launch_plain_ell(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c, uint32_t p,
+                           int s, int ell, cudaStream_t st, DeviceWorkspace* ws) {
+    const int ni = (int)n, mi = (int)m;
+#define PM_ELL(W)                                                                   \
+    switch (s) {                                                                    \
+        case 1: return launch_pair_s<1, W>(a, ni, b, mi, c, p, st, ws);            \
+        case 2: return launch_pair_s<2, W>(a, ni, b, mi, c, p, st, ws);            \
+        case 4: return launch_pair_s<4, W>(a, ni, b, mi, c, p, st, ws);            \
+        case 8: return launch_pair_s<8, W>(a, ni, b, mi, c, p, st, ws);            \
+        case 16: return launch_pair_s<16, W>(a, ni, b, mi, c, p, st, ws);          \
+        case 32: return launch_pair_s<32, W>(a, ni, b, mi, c, p, st, ws);          \
+        case 64: return launch_pair_s<64, W>(a, ni, b, mi, c, p, st, ws);          \
+        default: return PM_ERR_INVALID_ARG;                                         \
+    }
+    if (ell == 128) PM_ELL(4)
+    if (ell == 512) PM_ELL(16)
+    if (ell == 32 * WB) return launch_plain(a, n, b, m, c, p, s, st, ws);
+#undef PM_ELL
+    return PM_ERR_INVALID_ARG;
+}
+#endif  // PM_PLAIN_STUDY_TU
 
 }  // namespace pm
 
+#ifndef PM_PLAIN_STUDY_TU
 // ---------------------------------------------------------------------------
 // polymul_plain_noalloc: the single-pair product of polymul_plain with its
 // scratch (partial-sum slots and tile counters) in a file-scope device array
@@ -1247,3 +1292,5 @@ extern "C" pm_status polymul_plain_noalloc(const uint32_t* a, int64_t deg_a, con
         default: return PM_ERR_INVALID_ARG;
     }
 }
+
+#endif  // PM_PLAIN_STUDY_TU

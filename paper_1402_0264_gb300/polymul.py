@@ -42,6 +42,7 @@ def _declare(lib):
         "polymul_plain": ([V, I64, V, I64, V, U32, INT, V], INT),
         "polymul_ntt": ([V, I64, V, I64, V, U32, U32, V], INT),
         "polymul_plain_noalloc": ([V, I64, V, I64, V, U32, INT, V], INT),
+        "polymul_plain_ell": ([V, I64, V, I64, V, U32, INT, INT, V], INT),
         "polymul_batched": ([I64, V, V, V, V, V, V, U32, INT, INT, I64, V], INT),
         "polymul_divide": ([V, I64, V, I64, V, V, U32, INT, V], INT),
         "polymul_model_predict": ([I64, I64, INT, INT, D, D, ctypes.POINTER(D)], INT),
@@ -118,6 +119,17 @@ def plain(a, b, p: int = P_DEFAULT, s: int = 0, out=None, stream=None):
         raise ValueError("out must hold len(a) + len(b) - 1 words")
     _check(lib().polymul_plain(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"), b.numel() - 1,
                                _dev_words(out, "out"), p, s, _stream_ptr(stream)), "polymul_plain")
+    return out
+
+
+def plain_ell(a, b, s: int, ell: int, p: int = P_DEFAULT, out=None, stream=None):
+    """plain() with l = ell threads per block (128, 256 or 512): the block-size study."""
+    L = a.numel() + b.numel() - 1
+    out = _alloc(L, a) if out is None else out
+    if out.numel() != L:
+        raise ValueError("out must hold len(a) + len(b) - 1 words")
+    _check(lib().polymul_plain_ell(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"), b.numel() - 1,
+                                   _dev_words(out, "out"), p, s, ell, _stream_ptr(stream)), "polymul_plain_ell")
     return out
 
 

@@ -112,3 +112,13 @@ def test_divide_validation_happens_on_host(lib):
     assert f(FAKE, 5, FAKE2, 3, Q, R, P, -1, NULL) == 1         # negative s
     assert f(FAKE, 5, FAKE2, 3, FAKE, R, P, 0, NULL) == 1       # q overlapping a
     assert f(FAKE, 5, FAKE2, 3, Q, Q, P, 0, NULL) == 1          # r overlapping q
+
+
+def test_plain_ell_validation_happens_on_host(lib):
+    f = lib.polymul_plain_ell
+    C = ctypes.c_void_p(0x30000000)
+    P = pm.P_DEFAULT
+    assert f(FAKE, 3, FAKE2, 3, C, P, 8, 200, NULL) == 1     # l not 128/256/512
+    assert f(FAKE, 3, FAKE2, 3, C, P, 0, 256, NULL) == 1     # s must be given
+    assert f(FAKE, 3, FAKE2, 3, C, P, 3, 128, NULL) == 1     # s not a power of two
+    assert f(NULL, 3, FAKE2, 3, C, P, 8, 512, NULL) == 1     # null input

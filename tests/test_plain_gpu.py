@@ -126,3 +126,13 @@ def test_tuner_picks_a_candidate():
     best, times = pm.tune_plain(dev(a), dev(b), reps=2)
     assert best in SS and best in times
     assert pm.default_s(len(a) - 1, len(b) - 1) == best
+
+
+@pytest.mark.parametrize("ell", [128, 512])
+@pytest.mark.parametrize("s", [1, 4, 8, 32, 64])
+def test_block_size_study(ell, s):
+    """polymul_plain_ell: the same words as the oracle for l = 128 and 512 threads per block."""
+    a, b = inputs.poly_pair(3000, 1700, inputs.SEED_BASE + 900 + s)
+    got = host(pm.plain_ell(dev(a), dev(b), s=s, ell=ell))
+    assert pm.sync_status() == 0
+    assert_equal(got, oracle.polymul(a, b, P), f"l={ell} s={s}")
