@@ -410,6 +410,27 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
                              "best_thm_s": min(sweep, key=lambda r: r["model_T_thm_s"])["s"],
                              "best_cor_s": min(sweep, key=lambda r: r["model_T_cor_s"])["s"]}
 
+    # --- block-size study: l = 128 and 512 threads per block beside l = 256 ---
+    ell_rows = {256: [{"s": r["s"], "ms": r["ms"], "model_T_thm_s": r["model_T_thm_s"],
+                       "model_T_cor_s": r["model_T_cor_s"]} for r in sweep]}
+    ref = c.clone()
+    for el in (128, 512):
+        u_el = el / (IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6)
+        pts = []
+        for s in pm.S_CANDIDATES:
+            ms = median_ms(lambda: pm.plain_ell(a, b, s, el, out=c), 20, flush, stream)
+            assert torch.equal(c, ref), f"l = {el}, s = {s} disagrees with l = 256"
+            pred = pm.model_predict(N_SINGLE, N_SINGLE, s, el, U, float(SMS))
+            pts.append({"s": s, "ms": ms, "model_T_thm_s": pred["T_thm"] * u_el,
+                        "model_T_cor_s": pred["T_cor"] * u_el})
+        ell_rows[el] = pts
+    best = {el: min(p_, key=lambda r: r["ms"]) for el, p_ in ell_rows.items()}
+    rows["plain_ell_study"] = {
+        "workload": "degree-16383 pair", "U": U, "P": SMS,
+        "points": {str(el): p_ for el, p_ in ell_rows.items()},
+        "best_measured": {str(el): {"s": r["s"], "ms": r["ms"]} for el, r in best.items()},
+        "best_thm": {str(el): min(p_, key=lambda r: r["model_T_thm_s"])["s"] for el, p_ in ell_rows.items()}}
+
     # --- degree-1023 pair (latency bound) ---
     a0, b0 = inputs.workload_small()
     da0, db0 = torch.from_numpy(a0).to(dev), torch.from_numpy(b0).to(dev)
