@@ -10,6 +10,8 @@ CPU-baseline leg of ``bench.py`` may import this package.  The library in
   exact evaluator).
 * ``divide``/``invmod``: Euclidean division a = q b + r over Z/pZ (Section 3),
   one division step at a time from the top as in Algorithm 1.
+* ``gcd``: the monic greatest common divisor over Z/pZ (Section 6), by the
+  textbook remainder sequence.
 * ``model``: the printed cost formulas of Section 5 and the Graham-Brent bound
   of Section 2.4 (Theorem 1, Corollary 1), in fp64.
 """
@@ -75,6 +77,9 @@ def _load():
             lib.oracle_divide.argtypes = [_u32p, ctypes.c_int64, _u32p, ctypes.c_int64, ctypes.c_uint32,
                                           _u32p, _u32p]
             lib.oracle_divide.restype = ctypes.c_int
+            lib.oracle_gcd.argtypes = [_u32p, ctypes.c_int64, _u32p, ctypes.c_int64, ctypes.c_uint32,
+                                       _u32p, _i64p]
+            lib.oracle_gcd.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -172,3 +177,18 @@ def divide(a, b, p: int):
     if rc != 0:
         raise MemoryError("oracle_divide")
     return q, r
+
+
+def gcd(a, b, p: int):
+    """The monic gcd of a and b over Z/pZ, p prime (Section 6), as a uint32 array of deg + 1
+    words; an empty array when a = b = 0.  Leading zero coefficients are allowed."""
+    a, b = _u32(a), _u32(b)
+    g = np.zeros(max(len(a), len(b), 1), dtype=np.uint32)
+    deg = ctypes.c_int64(-1)
+    rc = _load().oracle_gcd(_p(a, _u32p), len(a), _p(b, _u32p), len(b), p, _p(g, _u32p),
+                            ctypes.byref(deg))
+    if rc == -2:
+        raise ValueError("oracle_gcd: a leading coefficient has no inverse mod p")
+    if rc != 0:
+        raise MemoryError("oracle_gcd")
+    return g[: deg.value + 1].copy()

@@ -29,6 +29,10 @@
  *                             steps of Algorithms 1-4, one leading
  *                             coefficient cancelled per step, done here one
  *                             step at a time)
+ *   oracle_gcd                the monic greatest common divisor over Z/pZ
+ *                             (Section 6, "Euclidean algorithm"), computed
+ *                             here by the textbook remainder sequence
+ *                             r_{i+1} = r_{i-1} mod r_i, then made monic
  *
  * Plain C, single threaded, unoptimised on purpose.
  */
@@ -208,5 +212,61 @@ int oracle_divide(const uint32_t *a, int64_t n, const uint32_t *b, int64_t m, ui
     }
     for (int64_t i = 0; i < m - 1; ++i) r[i] = rem[i];
     free(rem);
+    return 0;
+}
+
+/* Degree of x (terms 0..len-1) once its zero leading coefficients are
+ * dropped; -1 for the zero polynomial. */
+static int64_t true_degree(const uint32_t *x, int64_t len) {
+    int64_t d = len - 1;
+    while (d >= 0 && x[d] == 0) --d;
+    return d;
+}
+
+/* The greatest common divisor of a (na terms) and b (nb terms) over
+ * Z/pZ, p prime (Section 6): the Euclidean remainder sequence
+ * r_0 = a, r_1 = b, r_{i+1} = r_{i-1} mod r_i until the remainder is
+ * zero; the last nonzero r_i, divided by its leading coefficient, is the
+ * gcd.  Leading zero coefficients of the inputs are allowed.  Writes the
+ * monic gcd to g[0..deg] and its degree to *deg_g (-1 when a = b = 0, g
+ * untouched then); g must hold max(na, nb) words.  Returns 0, -1 for bad
+ * sizes, -2 when a leading coefficient has no inverse mod p, -3 when out of
+ * memory. */
+int oracle_gcd(const uint32_t *a, int64_t na, const uint32_t *b, int64_t nb, uint32_t p,
+               uint32_t *g, int64_t *deg_g) {
+    if (na < 0 || nb < 0) return -1;
+    int64_t cap = (na > nb ? na : nb) + 1;
+    uint32_t *u = (uint32_t *)calloc((size_t)cap, sizeof(uint32_t));
+    uint32_t *v = (uint32_t *)calloc((size_t)cap, sizeof(uint32_t));
+    if (!u || !v) { free(u); free(v); return -3; }
+    for (int64_t i = 0; i < na; ++i) u[i] = a[i] % p;
+    for (int64_t i = 0; i < nb; ++i) v[i] = b[i] % p;
+    int64_t du = true_degree(u, na), dv = true_degree(v, nb);
+    while (dv >= 0) {
+        /* u <- u mod v: cancel the leading coefficient of u while deg u >= deg v */
+        uint32_t inv = oracle_invmod(v[dv], p);
+        if (inv == 0) { free(u); free(v); return -2; }
+        while (du >= dv) {
+            uint32_t c = mulmod(u[du], inv, p);
+            int64_t shift = du - dv;
+            for (int64_t j = 0; j <= dv; ++j) {
+                uint32_t t = mulmod(c, v[j], p);
+                uint32_t *x = &u[shift + j];
+                *x = *x >= t ? *x - t : *x + p - t;
+            }
+            du = true_degree(u, du + 1);
+        }
+        /* (u, v) <- (v, u mod v) */
+        uint32_t *w = u; u = v; v = w;
+        int64_t dw = du; du = dv; dv = dw;
+    }
+    *deg_g = du;
+    if (du >= 0) {
+        uint32_t inv = oracle_invmod(u[du], p);
+        if (inv == 0) { free(u); free(v); return -2; }
+        for (int64_t i = 0; i <= du; ++i) g[i] = mulmod(u[i], inv, p);
+    }
+    free(u);
+    free(v);
     return 0;
 }
