@@ -5,7 +5,8 @@ job; here the oracle runs only in the cpu_baseline leg (which also compares
 its product with the GPU's headline result word for word) and in the
 reference arm, and every other result is cross-checked on the GPU (plain
 against transform, tensor-core against plain, graph against direct, a
-division against a = q b + r, a transform product at a random point).
+division against a = q b + r, a gcd against its planted factor, a transform
+product at a random point).
 
 Headline step: one product of a degree-16383 pair (n = m = 16384, so
 n*m = 2^28 modular multiply-adds) by the s-blocked plain kernel at the tuned
@@ -596,6 +597,46 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
                         "naive_vs_s256_deg4095_by_2047": {"ms_s1": small[1], "ms_s256": small[256],
                                                          "measured_ratio": small[1] / small[256],
                                                          "model_ratio_T1_over_Ts": T1 / Ts, "U": U}}
+
+    # --- gcd (Section 6, Algorithms 10-11): a of degree 9999, b of degree 8999, planted gcd of degree 1000 ---
+    def planted_on_gpu(g_np, u_np, w_np):
+        """b = g u and a = g (u w + 1) formed by the library's own product."""
+        tg, tu, tw = (torch.from_numpy(x).to(dev) for x in (g_np, u_np, w_np))
+        v = pm.plain(tu, tw).cpu().numpy()
+        v[0] = (int(v[0]) + 1) % P
+        return pm.plain(tg, torch.from_numpy(v).to(dev)), pm.plain(tg, tu), tg
+
+    g_np, u_np, w_np = inputs.workload_gcd()
+    ga, gb, tg = planted_on_gpu(g_np, u_np, w_np)
+    gout = torch.empty(max(ga.numel(), gb.numel()), dtype=torch.uint32, device=dev)
+    steps_g = (ga.numel() - 1 - 1000) + (gb.numel() - 1 - 1000)  # each step lowers one degree by one
+    sweep = []
+    for s_g in (32, 64, 128, 256):
+        res = pm.gcd(ga, gb, s=s_g, out=gout)
+        assert pm.sync_status() == 0 and torch.equal(res, tg), f"gcd s={s_g}: not the planted gcd"
+        ms = median_ms(lambda s_g=s_g: pm.gcd(ga, gb, s=s_g, out=gout), 5, flush, stream)
+        sweep.append({"s": s_g, "ms": ms, "us_per_step": ms * 1e3 / steps_g})
+    # s = 1 (the naive gcd of Algorithms 8-9, one step per launch) against s = 256 on the smallest size of
+    # the paper's gcd timings (degrees 1999 and 1499), with the running-time ratio T_1 / T_s of Corollary 1
+    # and the costs of Section 6 (N_1 / K_1 = n + l + 1, L_1 = n + m - 2, C_1 = 3 + 5U;
+    # N_s / K_s = n / s + 1, L_s = (n + m) / s, C_s = 3 s + 8 U)
+    g1, u1, w1 = inputs.gcd_factors(200, 1299, 500, inputs.SEED_BASE + 8)
+    sa, sb, sg = planted_on_gpu(g1, u1, w1)
+    sout = torch.empty(max(sa.numel(), sb.numel()), dtype=torch.uint32, device=dev)
+    small = {}
+    for s_g in (1, 256):
+        res = pm.gcd(sa, sb, s=s_g, out=sout)
+        assert pm.sync_status() == 0 and torch.equal(res, sg), f"gcd s={s_g}: not the planted gcd"
+        small[s_g] = median_ms(lambda s_g=s_g: pm.gcd(sa, sb, s=s_g, out=sout), 3, flush, stream)
+    n_g, m_g, ell_g, s_m = sa.numel(), sb.numel(), 256, 256
+    T1g = (n_g + ell_g + 1 + n_g + m_g - 2) * (3 + 5 * U)
+    Tsg = (n_g / s_m + 1 + (n_g + m_g) / s_m) * (3 * s_m + 8 * U)
+    rows["gcd"] = {"workload": "a of degree 9999, b of degree 8999, planted gcd of degree 1000",
+                   "division_steps": steps_g, "s_sweep": sweep,
+                   "best_s": min(sweep, key=lambda e: e["ms"])["s"],
+                   "naive_vs_s256_deg1999_and_1499": {"ms_s1": small[1], "ms_s256": small[256],
+                                                      "measured_ratio": small[1] / small[256],
+                                                      "model_ratio_T1_over_Ts": T1g / Tsg, "U": U}}
     return rows
 
 
@@ -634,6 +675,19 @@ def run_case(args):
             qb[: out.numel()] = (qb[: out.numel()] + out.cpu().numpy().astype(np.uint64)) % P
             return np.array_equal(qb.astype(np.uint32), a)
         macs, name = (len(a) - len(b) + 1) * len(b), "degree 32767 divided by degree 16383, s=%d" % sd
+    elif args.case == "gcd":
+        g_np, u_np, w_np = inputs.workload_gcd()
+        tg, tu, tw = (torch.from_numpy(x).to(dev) for x in (g_np, u_np, w_np))
+        v = pm.plain(tu, tw).cpu().numpy()
+        v[0] = (int(v[0]) + 1) % P
+        ta, tb = pm.plain(tg, torch.from_numpy(v).to(dev)), pm.plain(tg, tu)
+        out = torch.empty(max(ta.numel(), tb.numel()), dtype=torch.uint32, device=dev)
+        sg = args.s or 0
+        res = {}
+        def step():
+            res["g"] = pm.gcd(ta, tb, s=sg, out=out)
+        check = lambda: torch.equal(res["g"], tg)  # the planted factor
+        macs, name = 0, "gcd of degrees 9999 and 8999 (planted gcd of degree 1000), s=%d" % sg
     elif args.case == "ntt":
         a, b = inputs.workload_ntt()
         ta, tb = torch.from_numpy(a).to(dev), torch.from_numpy(b).to(dev)
@@ -673,7 +727,8 @@ def run_case(args):
     assert pm.sync_status() == 0
     ms = sum(ts) / len(ts)
     print(json.dumps({"case": args.case, "workload": name, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": ms, "macs_per_s": macs / (ms * 1e-3), "unit": UNIT}), flush=True)
+                      "ms_per_step": ms, "macs_per_s": macs / (ms * 1e-3) if macs else None, "unit": UNIT}),
+          flush=True)
     return 0
 
 
@@ -704,7 +759,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--s", type=int, default=0, help="fix the block parameter (skip the tuner)")
-    ap.add_argument("--case", choices=["plain", "batched", "tensor", "ntt", "divide"], default=None,
+    ap.add_argument("--case", choices=["plain", "batched", "tensor", "ntt", "divide", "gcd"], default=None,
                     help="time one kernel family alone (profiling runs); prints one JSON line")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -194,6 +194,35 @@ pm_status polymul_divide(const uint32_t *a, int64_t deg_a, const uint32_t *b, in
                          uint32_t *q, uint32_t *r, uint32_t p, int s, void *stream);
 
 /*
+ * polymul_gcd - the monic greatest common divisor over Z/pZ (Section 6,
+ * "The Euclidean algorithm for polynomials", Algorithms 10-11 with parameter
+ * s; s = 1 is the naive gcd of Algorithms 8-9, one division step per launch).
+ *
+ *   a, deg_a   device array of deg_a+1 coefficients (0 <= deg_a <= PM_MAX_DEG);
+ *              leading zeros allowed, words are taken mod p
+ *   b, deg_b   the same for b; a = 0 or b = 0 is allowed
+ *   g          device array of max(deg_a, deg_b)+1 words, written in full: the
+ *              monic gcd in g[0 .. *deg_g], zeros above it (all zeros when
+ *              a = b = 0)
+ *   deg_g      host pointer: the degree of the gcd, -1 when a = b = 0
+ *   p          prime, 2 <= p < PM_MAX_P (primality is not checked; a leading
+ *              coefficient without an inverse sets PM_ERR_INVALID_ARG in the
+ *              status word)
+ *   s          division steps per launch, 1 <= s <= 256; 0 picks 128
+ *   stream     cudaStream_t as void*
+ * The number of division steps (at most deg_a + deg_b + 2) depends on the
+ * data, so the call launches rounds of s steps in batches and reads a
+ * 48-byte state back after each batch: it synchronises `stream` and cannot
+ * be captured into a CUDA graph (PM_ERR_UNSUPPORTED while capturing).
+ * Scratch: 8 (deg_a + deg_b + 2) bytes plus 1 KiB per (device, stream).
+ * Returns PM_OK, PM_ERR_INVALID_ARG (null pointer, degrees, s, g overlapping
+ * an input), PM_ERR_RANGE (p), PM_ERR_UNSUPPORTED, PM_ERR_NOMEM,
+ * PM_ERR_INTERNAL or PM_ERR_CUDA.
+ */
+pm_status polymul_gcd(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b, uint32_t *g,
+                      int64_t *deg_g, uint32_t p, int s, void *stream);
+
+/*
  * polymul_model_predict - the cost model of the s-blocked product
  * (Section 5 printed formulas; Theorem 1 and Corollary 1 of Section 2.4).
  * Host-only; no GPU needed.

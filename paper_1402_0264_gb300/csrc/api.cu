@@ -2,6 +2,7 @@
 // workspace, the device status word, the autotuner cache and the cost model.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <map>
@@ -224,6 +225,22 @@ pm_status polymul_divide(const uint32_t* a, int64_t deg_a, const uint32_t* b, in
     return launch_divide(a, deg_a + 1, b, deg_b + 1, q, r, p, s, (cudaStream_t)stream, ws);
 }
 
+pm_status polymul_gcd(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64_t deg_b, uint32_t* g,
+                      int64_t* deg_g, uint32_t p, int s, void* stream) {
+    if (!a || !b || !g || !deg_g) return PM_ERR_INVALID_ARG;
+    if (deg_a < 0 || deg_b < 0 || deg_a > PM_MAX_DEG || deg_b > PM_MAX_DEG) return PM_ERR_INVALID_ARG;
+    if (p < 2 || p >= PM_MAX_P) return PM_ERR_RANGE;
+    if (s < 0 || s > 256) return PM_ERR_INVALID_ARG;
+    const int64_t ng = std::max(deg_a, deg_b) + 1;
+    if (overlaps(g, ng, a, deg_a + 1) || overlaps(g, ng, b, deg_b + 1)) return PM_ERR_INVALID_ARG;
+    if (is_capturing(stream)) return PM_ERR_UNSUPPORTED;  // the call reads its state back between rounds
+    if (s == 0) s = 128;
+    pm_status rc = PM_OK;
+    DeviceWorkspace* ws = workspace(stream, &rc);
+    if (!ws) return rc;
+    return launch_gcd(a, deg_a + 1, b, deg_b + 1, g, deg_g, p, s, (cudaStream_t)stream, ws);
+}
+
 pm_status polymul_batched(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                           const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                           const int64_t* c_off, uint32_t p, int mode, int s, int64_t max_deg,
@@ -355,6 +372,7 @@ pm_status polymul_release(void) {
             if (sc->tc) cudaFree(sc->tc);
             if (sc->ntt) cudaFree(sc->ntt);
             if (sc->div) cudaFree(sc->div);
+            if (sc->gcd) cudaFree(sc->gcd);
             delete sc;
         }
         delete mp;

@@ -85,6 +85,8 @@ struct StreamScratch {
     size_t ntt_bytes = 0;
     void* div = nullptr;           // division: working copy of the dividend, inverse of lc(b)
     size_t div_bytes = 0;
+    void* gcd = nullptr;           // gcd: round states and two copies of both polynomials
+    size_t gcd_bytes = 0;
 };
 
 // Per-device state owned by the library.
@@ -131,5 +133,7 @@ pm_status launch_plain_ell(const uint32_t* a, int64_t n, const uint32_t* b, int6
                            int s, int ell, cudaStream_t st, DeviceWorkspace* ws);
 pm_status launch_divide(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* q, uint32_t* r,
                         uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws);
+pm_status launch_gcd(const uint32_t* a, int64_t na, const uint32_t* b, int64_t nb, uint32_t* g, int64_t* deg_g,
+                     uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws);
 
 }  // namespace pm

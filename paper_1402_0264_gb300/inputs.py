@@ -134,3 +134,22 @@ def workload_tensor(batch: int = 1024, deg: int = 4095, p: int = P_DEFAULT,
 def workload_ntt(deg: int = 2**22 - 1, p: int = P_DEFAULT, seed: int = SEED_BASE + 4):
     """One pair of degree `deg` (2^22 - 1 by default)."""
     return poly_pair(deg, deg, seed, p)
+
+
+def gcd_factors(deg_g: int, deg_u: int, deg_w: int, seed: int, p: int = P_DEFAULT):
+    """Factors of a planted gcd: g monic of degree deg_g and u, w uniform with nonzero leading
+    coefficients.  The gcd workload is b = g u and a = g (u w + 1), whose gcd is exactly g
+    (gcd(u w + 1, u) = 1); each side forms those products with its own code."""
+    g = uniform_mod(seed, 21, deg_g + 1, p)
+    g[-1] = 1
+    u = uniform_mod(seed, 22, deg_u + 1, p)
+    w = uniform_mod(seed, 23, deg_w + 1, p)
+    u[-1] = u[-1] if u[-1] else 1
+    w[-1] = w[-1] if w[-1] else 1
+    return g, u, w
+
+
+def workload_gcd(p: int = P_DEFAULT, seed: int = SEED_BASE + 7):
+    """Factors for a of degree 9999 and b of degree 8999 with a gcd of degree 1000 (the largest
+    size of the paper's gcd timings, Section 6): deg g = 1000, deg u = 7999, deg w = 1000."""
+    return gcd_factors(1000, 7999, 1000, seed, p)

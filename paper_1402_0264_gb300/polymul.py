@@ -45,6 +45,7 @@ def _declare(lib):
         "polymul_plain_ell": ([V, I64, V, I64, V, U32, INT, INT, V], INT),
         "polymul_batched": ([I64, V, V, V, V, V, V, U32, INT, INT, I64, V], INT),
         "polymul_divide": ([V, I64, V, I64, V, V, U32, INT, V], INT),
+        "polymul_gcd": ([V, I64, V, I64, V, ctypes.POINTER(I64), U32, INT, V], INT),
         "polymul_model_predict": ([I64, I64, INT, INT, D, D, ctypes.POINTER(D)], INT),
         "polymul_tune_plain": ([V, I64, V, I64, V, U32, INT, V, ctypes.POINTER(INT),
                                 ctypes.POINTER(ctypes.c_float)], INT),
@@ -184,6 +185,20 @@ def divide(a, b, p: int = P_DEFAULT, s: int = 0, q=None, r=None, stream=None):
     _check(lib().polymul_divide(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"), b.numel() - 1,
                                 _dev_words(q, "q"), rp, p, s, _stream_ptr(stream)), "polymul_divide")
     return q, r
+
+
+def gcd(a, b, p: int = P_DEFAULT, s: int = 0, out=None, stream=None):
+    """The monic gcd of a and b over Z/pZ, p prime (Section 6); s division steps per launch.
+    Returns a view of the first deg + 1 words of `out` (max(len(a), len(b)) words); synchronises
+    the stream."""
+    n = max(a.numel(), b.numel())
+    out = _alloc(n, a) if out is None else out
+    if out.numel() != n:
+        raise ValueError("out must hold max(len(a), len(b)) words")
+    deg = ctypes.c_int64(-2)
+    _check(lib().polymul_gcd(_dev_words(a, "a"), a.numel() - 1, _dev_words(b, "b"), b.numel() - 1,
+                             _dev_words(out, "out"), ctypes.byref(deg), p, s, _stream_ptr(stream)), "polymul_gcd")
+    return out[: deg.value + 1]
 
 
 def model_predict(n: int, m: int, s: int, ell: int, U: float, P: float) -> dict:

@@ -122,3 +122,21 @@ def test_plain_ell_validation_happens_on_host(lib):
     assert f(FAKE, 3, FAKE2, 3, C, P, 0, 256, NULL) == 1     # s must be given
     assert f(FAKE, 3, FAKE2, 3, C, P, 3, 128, NULL) == 1     # s not a power of two
     assert f(NULL, 3, FAKE2, 3, C, P, 8, 512, NULL) == 1     # null input
+
+
+def test_gcd_validation_happens_on_host(lib):
+    f = lib.polymul_gcd
+    G = ctypes.c_void_p(0x30000000)
+    P = pm.P_DEFAULT
+    deg = ctypes.c_int64(0)
+    dp = ctypes.byref(deg)
+    assert f(NULL, 5, FAKE2, 3, G, dp, P, 0, NULL) == 1         # null input
+    assert f(FAKE, 5, FAKE2, 3, G, None, P, 0, NULL) == 1       # null degree output
+    assert f(FAKE, -1, FAKE2, 3, G, dp, P, 0, NULL) == 1        # negative degree
+    assert f(FAKE, 5, FAKE2, 2**30, G, dp, P, 0, NULL) == 1     # degree too large
+    assert f(FAKE, 5, FAKE2, 3, G, dp, 1, 0, NULL) == 2         # p < 2
+    assert f(FAKE, 5, FAKE2, 3, G, dp, 2**30, 0, NULL) == 2     # p too large
+    assert f(FAKE, 5, FAKE2, 3, G, dp, P, 257, NULL) == 1       # s too large
+    assert f(FAKE, 5, FAKE2, 3, G, dp, P, -1, NULL) == 1        # negative s
+    assert f(FAKE, 5, FAKE2, 3, FAKE, dp, P, 0, NULL) == 1      # g overlapping a
+    assert f(FAKE, 5, FAKE2, 3, FAKE2, dp, P, 0, NULL) == 1     # g overlapping b
