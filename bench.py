@@ -599,17 +599,16 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
                                                          "model_ratio_T1_over_Ts": T1 / Ts, "U": U}}
 
     # --- gcd (Section 6, Algorithms 10-11): a of degree 9999, b of degree 8999, planted gcd of degree 1000 ---
-    def planted_on_gpu(g_np, u_np, w_np):
-        """b = g u and a = g (u w + 1) formed by the library's own product."""
-        tg, tu, tw = (torch.from_numpy(x).to(dev) for x in (g_np, u_np, w_np))
-        v = pm.plain(tu, tw).cpu().numpy()
-        v[0] = (int(v[0]) + 1) % P
-        return pm.plain(tg, torch.from_numpy(v).to(dev)), pm.plain(tg, tu), tg
+    def planted_on_gpu(g_np, u_np, v_np):
+        """a = g u and b = g v formed by the library's own product (gcd(u, v) = 1 for these seeds)."""
+        tg, tu, tv = (torch.from_numpy(x).to(dev) for x in (g_np, u_np, v_np))
+        return pm.plain(tg, tu), pm.plain(tg, tv), tg
 
-    g_np, u_np, w_np = inputs.workload_gcd()
-    ga, gb, tg = planted_on_gpu(g_np, u_np, w_np)
+    g_np, u_np, v_np = inputs.workload_gcd()
+    ga, gb, tg = planted_on_gpu(g_np, u_np, v_np)
     gout = torch.empty(max(ga.numel(), gb.numel()), dtype=torch.uint32, device=dev)
-    steps_g = (ga.numel() - 1 - 1000) + (gb.numel() - 1 - 1000)  # each step lowers one degree by one
+    # the normal remainder sequence lowers one degree by one per step, from (9999, 8999) to (1000, -1)
+    steps_g = (ga.numel() - 1 - 1000) + (gb.numel() - 1 - 1000) + 1
     sweep = []
     for s_g in (32, 64, 128, 256):
         res = pm.gcd(ga, gb, s=s_g, out=gout)
@@ -620,8 +619,8 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
     # the paper's gcd timings (degrees 1999 and 1499), with the running-time ratio T_1 / T_s of Corollary 1
     # and the costs of Section 6 (N_1 / K_1 = n + l + 1, L_1 = n + m - 2, C_1 = 3 + 5U;
     # N_s / K_s = n / s + 1, L_s = (n + m) / s, C_s = 3 s + 8 U)
-    g1, u1, w1 = inputs.gcd_factors(200, 1299, 500, inputs.SEED_BASE + 8)
-    sa, sb, sg = planted_on_gpu(g1, u1, w1)
+    g1, u1, v1 = inputs.gcd_cofactors(200, 1799, 1299, inputs.SEED_BASE + 8)
+    sa, sb, sg = planted_on_gpu(g1, u1, v1)
     sout = torch.empty(max(sa.numel(), sb.numel()), dtype=torch.uint32, device=dev)
     small = {}
     for s_g in (1, 256):
@@ -676,11 +675,9 @@ def run_case(args):
             return np.array_equal(qb.astype(np.uint32), a)
         macs, name = (len(a) - len(b) + 1) * len(b), "degree 32767 divided by degree 16383, s=%d" % sd
     elif args.case == "gcd":
-        g_np, u_np, w_np = inputs.workload_gcd()
-        tg, tu, tw = (torch.from_numpy(x).to(dev) for x in (g_np, u_np, w_np))
-        v = pm.plain(tu, tw).cpu().numpy()
-        v[0] = (int(v[0]) + 1) % P
-        ta, tb = pm.plain(tg, torch.from_numpy(v).to(dev)), pm.plain(tg, tu)
+        g_np, u_np, v_np = inputs.workload_gcd()
+        tg, tu, tv = (torch.from_numpy(x).to(dev) for x in (g_np, u_np, v_np))
+        ta, tb = pm.plain(tg, tu), pm.plain(tg, tv)
         out = torch.empty(max(ta.numel(), tb.numel()), dtype=torch.uint32, device=dev)
         sg = args.s or 0
         res = {}

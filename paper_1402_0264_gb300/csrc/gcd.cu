@@ -29,7 +29,10 @@
 // the paper's a - lc(a) lc(b)^-1 x^d b but is a unit multiple of it, so the
 // sequence of degrees and the gcd up to a unit are the same, and no modular
 // inverse sits on the sequential path; one inverse at the end makes the
-// result monic.  A polynomial that becomes a nonzero constant ends the
+// result monic.  For odd p each step's words are reduced by Montgomery's
+// method (P. Montgomery, "Modular multiplication without trial division",
+// Math. Comp. 1985) without converting to Montgomery form, which scales the
+// step by the unit 2^-32 mod p and leaves degrees and the gcd unchanged.  A polynomial that becomes a nonzero constant ends the
 // computation with gcd 1 (the paper's test "zero or constant" would return
 // the other polynomial there).
 //
@@ -65,10 +68,25 @@ struct GcdState {
 };
 static_assert(sizeof(GcdState) == 48, "GcdState layout");
 
-// c1 x + c2n y mod p for words below 2^32 and c1, c2n < p < 2^30.
-__device__ __forceinline__ uint32_t gcd_comb(uint32_t c1, uint32_t x, uint32_t c2n, uint32_t y, uint32_t p,
-                                             uint64_t mu) {
-    return barrett((uint64_t)c1 * x + (uint64_t)c2n * y, p, mu);
+struct GcdMod {
+    uint32_t p;
+    uint32_t pinv;   // -p^-1 mod 2^32 (odd p)
+    uint64_t mu;     // floor(2^64 / p)
+};
+
+// For x, y, c1, c2n < p < 2^30: MONT (odd p) gives (c1 x + c2n y) 2^-32 mod p
+// (v = c1 x + c2n y < 2p^2; q = v (-p^-1) mod 2^32 makes v + q p a multiple of
+// 2^32, and (v + q p) / 2^32 < 2p^2 / 2^32 + p < 2p); otherwise
+// (c1 x + c2n y) mod p by Barrett's method.
+template <bool MONT>
+__device__ __forceinline__ uint32_t gcd_comb(uint32_t c1, uint32_t x, uint32_t c2n, uint32_t y, const GcdMod& m) {
+    const uint64_t v = (uint64_t)c1 * x + (uint64_t)c2n * y;
+    if (MONT) {
+        const uint32_t q = (uint32_t)v * m.pinv;
+        const uint32_t r = (uint32_t)((v + (uint64_t)q * m.p) >> 32);
+        return r >= m.p ? r - m.p : r;
+    }
+    return barrett(v, m.p, m.mu);
 }
 
 // Copies a and b reduced mod p into the first copy of the arrays and writes
@@ -111,10 +129,12 @@ __device__ __forceinline__ uint32_t gcd_strip(const uint32_t* h, int& u, int lim
 
 // One round.  X* are the arrays at the round's start, Y* receive the result;
 // sin/sout the state copies; ybuf names Y's copy for the final state.
+template <bool MONT>
 __global__ void __launch_bounds__(GCD_THREADS) gcd_round_kernel(
     const uint32_t* __restrict__ XA, const uint32_t* __restrict__ XB, uint32_t* __restrict__ YA,
     uint32_t* __restrict__ YB, const GcdState* __restrict__ sin, GcdState* __restrict__ sout, int s, int H,
-    int ybuf, uint32_t p, uint64_t mu) {
+    int ybuf, GcdMod md) {
+    const uint32_t p = md.p;
     __shared__ uint32_t hA[GCD_HMAX], hB[GCD_HMAX];
     __shared__ uint32_t rc1[GCD_SMAX], rc2[GCD_SMAX];
     __shared__ int rsig[GCD_SMAX];       // (shift << 1) | (1 when b is the reduced one)
@@ -148,43 +168,78 @@ __global__ void __launch_bounds__(GCD_THREADS) gcd_round_kernel(
             hB[j] = db0 - j >= 0 ? XB[db0 - j] : 0u;
         }
         __syncwarp();
-        // offsets of the leading coefficients, exact head lengths
+        // offsets (from the round's tops) of the leading coefficients and exact head lengths; the
+        // degrees are below 2^30, so offsets and the test deg a >= deg b <=> ua - ub <= da0 - db0 fit
+        // 32-bit integers
+        const int Da = (int)da0, Db = (int)db0, D0 = Da - Db;
         int ua = 0, ub = 0, va = H, vb = H;
-        uint32_t la = 0, lb = 0;
-        bool need_a = true, need_b = true;
+        uint32_t la = gcd_strip(hA, ua, min(va, Da + 1), lane);
+        uint32_t lb = gcd_strip(hB, ub, min(vb, Db + 1), lane);
         int k = 0, kind = -1;
         int64_t dg = -1;
         for (int guard = 0; guard < GCD_SMAX + 2; ++guard) {
-            const int lim_a = (int)(da0 + 1 < (int64_t)va ? da0 + 1 : (int64_t)va);
-            const int lim_b = (int)(db0 + 1 < (int64_t)vb ? db0 + 1 : (int64_t)vb);
-            if (need_a) { la = gcd_strip(hA, ua, lim_a, lane); need_a = false; }
-            if (need_b) { lb = gcd_strip(hB, ub, lim_b, lane); need_b = false; }
-            const bool a_zero = ua > da0, b_zero = ub > db0;
+            const bool a_zero = ua > Da, b_zero = ub > Db;
             if ((!a_zero && ua >= va) || (!b_zero && ub >= vb)) break;   // head exhausted: next round
-            const int64_t da = a_zero ? -1 : da0 - ua, db = b_zero ? -1 : db0 - ub;
-            if (da < 0 && db < 0) { kind = GCD_IS_ZERO; dg = -1; break; }
-            if (da < 0) { kind = GCD_IS_B; dg = db; break; }
-            if (db < 0) { kind = GCD_IS_A; dg = da; break; }
-            if (da == 0 || db == 0) { kind = GCD_IS_ONE; dg = 0; break; }
+            if (a_zero || b_zero) {
+                kind = a_zero ? (b_zero ? GCD_IS_ZERO : GCD_IS_B) : GCD_IS_A;
+                dg = a_zero ? (b_zero ? -1 : Db - ub) : Da - ua;
+                break;
+            }
+            if (ua == Da || ub == Db) { kind = GCD_IS_ONE; dg = 0; break; }   // a nonzero constant
             if (k == s) break;
             const int sig = ub - ua;
-            if (da >= db) {
-                // a <- lc(b) a - lc(a) x^(da-db) b on the head: a[ua+j] pairs with b[ub+j]
+            if (ua - ub <= D0) {
+                // a <- lc(b) a - lc(a) x^(deg a - deg b) b on the head: a[ua+j] pairs with b[ub+j].
+                // Entries past what the remaining steps can reach (plus GCD_HEXTRA) are left stale
+                // and count as unknown: a round whose degrees drop that far ends early instead.
                 const uint32_t c1 = lb, c2n = p - la;
-                const int va_new = min(va, ua + vb - ub);
-                for (int i = ua + 1 + lane; i < va_new; i += 32) hA[i] = gcd_comb(c1, hA[i], c2n, hB[i + sig], p, mu);
+                const int va_new = min(min(va, ua + vb - ub), ua + (s - k) + GCD_HEXTRA);
+                // the next 32 entries first: the new leading coefficient is the first nonzero one
+                const int i0h = ua + 1 + lane;
+                uint32_t v = 0u;
+                if (i0h < va_new) {
+                    v = gcd_comb<MONT>(c1, hA[i0h], c2n, hB[i0h + sig], md);
+                    hA[i0h] = v;
+                }
+                const unsigned msk = __ballot_sync(0xffffffffu, v != 0u);
+                const int f = __ffs(msk) - 1;
+                const uint32_t lnew = __shfl_sync(0xffffffffu, v, f < 0 ? 0 : f);
+#pragma unroll 4
+                for (int i = i0h + 32; i < va_new; i += 32) hA[i] = gcd_comb<MONT>(c1, hA[i], c2n, hB[i + sig], md);
                 if (lane == 0) { rc1[k] = c1; rc2[k] = c2n; rsig[k] = sig * 2; }
                 va = va_new;
-                ua += 1;
-                need_a = true;
+                if (msk) {
+                    ua += 1 + f;
+                    la = lnew;
+                } else {   // 32 zeros: strip on from the entries the loop above wrote
+                    ua = min(ua + 33, min(va, Da + 1));
+                    __syncwarp();
+                    la = gcd_strip(hA, ua, min(va, Da + 1), lane);
+                }
             } else {
                 const uint32_t c1 = la, c2n = p - lb;
-                const int vb_new = min(vb, ub + va - ua);
-                for (int i = ub + 1 + lane; i < vb_new; i += 32) hB[i] = gcd_comb(c1, hB[i], c2n, hA[i - sig], p, mu);
+                const int vb_new = min(min(vb, ub + va - ua), ub + (s - k) + GCD_HEXTRA);
+                const int i0h = ub + 1 + lane;
+                uint32_t v = 0u;
+                if (i0h < vb_new) {
+                    v = gcd_comb<MONT>(c1, hB[i0h], c2n, hA[i0h - sig], md);
+                    hB[i0h] = v;
+                }
+                const unsigned msk = __ballot_sync(0xffffffffu, v != 0u);
+                const int f = __ffs(msk) - 1;
+                const uint32_t lnew = __shfl_sync(0xffffffffu, v, f < 0 ? 0 : f);
+#pragma unroll 4
+                for (int i = i0h + 32; i < vb_new; i += 32) hB[i] = gcd_comb<MONT>(c1, hB[i], c2n, hA[i - sig], md);
                 if (lane == 0) { rc1[k] = c1; rc2[k] = c2n; rsig[k] = sig * 2 + 1; }
                 vb = vb_new;
-                ub += 1;
-                need_b = true;
+                if (msk) {
+                    ub += 1 + f;
+                    lb = lnew;
+                } else {
+                    ub = min(ub + 33, min(vb, Db + 1));
+                    __syncwarp();
+                    lb = gcd_strip(hB, ub, min(vb, Db + 1), lane);
+                }
             }
             ++k;
             __syncwarp();
@@ -212,24 +267,31 @@ __global__ void __launch_bounds__(GCD_THREADS) gcd_round_kernel(
         ra[j] = t < hi ? wA[t] : 0u;
         rb[j] = t < hi ? wB[t] : 0u;
     }
+    const int nj = (hi - lo + GCD_THREADS - 1) / GCD_THREADS;   // slots in use (block-uniform)
     int prev = -1;
+    int code = K > 0 ? rsig[0] : 0;
+    uint32_t c1 = K > 0 ? rc1[0] : 0u, c2n = K > 0 ? rc2[0] : 0u;
     for (int k = 0; k < K; ++k) {
-        const int code = rsig[k];
         const int typ = code & 1;
         const int sig = code >> 1;   // arithmetic shift: floor, exact for even code - typ
-        const uint32_t c1 = rc1[k], c2n = rc2[k];
+        const uint32_t m1 = c1, m2 = c2n;
+        if (k + 1 < K) {             // the next step's record, ahead of its use
+            code = rsig[k + 1];
+            c1 = rc1[k + 1];
+            c2n = rc2[k + 1];
+        }
         if (typ != prev) {
             if (prev == 0) {
 #pragma unroll
                 for (int j = 0; j < GCD_J; ++j) {
                     const int t = lo + tid + j * GCD_THREADS;
-                    if (t < hi) wA[t] = ra[j];
+                    if (j < nj && t < hi) wA[t] = ra[j];
                 }
             } else if (prev == 1) {
 #pragma unroll
                 for (int j = 0; j < GCD_J; ++j) {
                     const int t = lo + tid + j * GCD_THREADS;
-                    if (t < hi) wB[t] = rb[j];
+                    if (j < nj && t < hi) wB[t] = rb[j];
                 }
             }
             __syncthreads();
@@ -238,21 +300,21 @@ __global__ void __launch_bounds__(GCD_THREADS) gcd_round_kernel(
         if (typ == 0) {
 #pragma unroll
             for (int j = 0; j < GCD_J; ++j) {
-                const int t = lo + tid + j * GCD_THREADS;
-                if (t < hi) {
+                if (j < nj) {
+                    const int t = lo + tid + j * GCD_THREADS;
                     const int tb = t + sig;
                     const uint32_t y = (tb >= 0 && tb < Wn) ? wB[tb] : 0u;
-                    ra[j] = gcd_comb(c1, ra[j], c2n, y, p, mu);
+                    if (t < hi) ra[j] = gcd_comb<MONT>(m1, ra[j], m2, y, md);
                 }
             }
         } else {
 #pragma unroll
             for (int j = 0; j < GCD_J; ++j) {
-                const int t = lo + tid + j * GCD_THREADS;
-                if (t < hi) {
+                if (j < nj) {
+                    const int t = lo + tid + j * GCD_THREADS;
                     const int ta = t - sig;
                     const uint32_t y = (ta >= 0 && ta < Wn) ? wA[ta] : 0u;
-                    rb[j] = gcd_comb(c1, rb[j], c2n, y, p, mu);
+                    if (t < hi) rb[j] = gcd_comb<MONT>(m1, rb[j], m2, y, md);
                 }
             }
         }
@@ -341,6 +403,12 @@ pm_status launch_gcd(const uint32_t* a, int64_t na, const uint32_t* b, int64_t n
     uint32_t* B[2] = {reinterpret_cast<uint32_t*>(base + 256 + 2 * wa),
                       reinterpret_cast<uint32_t*>(base + 256 + 2 * wa + wb)};
     const uint64_t mu = (uint64_t)(((unsigned __int128)1 << 64) / p);
+    GcdMod md{p, 0u, mu};
+    if (p & 1u) {
+        uint32_t inv = p;                       // Newton: each step doubles the correct low bits
+        for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
+        md.pinv = 0u - inv;
+    }
     const int H = s + GCD_HEXTRA;
     const int64_t nmax = std::max(na, nb);
     uint64_t launches = 0;
@@ -361,8 +429,12 @@ pm_status launch_gcd(const uint32_t* a, int64_t na, const uint32_t* b, int64_t n
         const unsigned blocks = (unsigned)std::max<int64_t>(1, (std::max(da, db) + GCD_T) / GCD_T);
         for (int64_t i = 0; i < batch; ++i, ++r) {
             const int x = (int)(r & 1), y = x ^ 1;
-            gcd_round_kernel<<<blocks, GCD_THREADS, 0, st>>>(A[x], B[x], A[y], B[y], state + x, state + y, s, H, y,
-                                                             p, mu);
+            if (p & 1u)
+                gcd_round_kernel<true><<<blocks, GCD_THREADS, 0, st>>>(A[x], B[x], A[y], B[y], state + x, state + y,
+                                                                       s, H, y, md);
+            else
+                gcd_round_kernel<false><<<blocks, GCD_THREADS, 0, st>>>(A[x], B[x], A[y], B[y], state + x, state + y,
+                                                                        s, H, y, md);
             e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(e);
             ++launches;

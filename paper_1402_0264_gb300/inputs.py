@@ -149,7 +149,21 @@ def gcd_factors(deg_g: int, deg_u: int, deg_w: int, seed: int, p: int = P_DEFAUL
     return g, u, w
 
 
+def gcd_cofactors(deg_g: int, deg_u: int, deg_v: int, seed: int, p: int = P_DEFAULT):
+    """g monic of degree deg_g and independent uniform u, v with nonzero leading coefficients:
+    a = g u and b = g v have gcd g whenever gcd(u, v) = 1 (true for all but a fraction of about
+    1/p of draws; a test checks it for the seeds used here).  Unlike gcd_factors, the Euclidean
+    algorithm on (a, b) then runs the normal remainder sequence, one degree at a time."""
+    g = uniform_mod(seed, 31, deg_g + 1, p)
+    g[-1] = 1
+    u = uniform_mod(seed, 32, deg_u + 1, p)
+    v = uniform_mod(seed, 33, deg_v + 1, p)
+    u[-1] = u[-1] if u[-1] else 1
+    v[-1] = v[-1] if v[-1] else 1
+    return g, u, v
+
+
 def workload_gcd(p: int = P_DEFAULT, seed: int = SEED_BASE + 7):
     """Factors for a of degree 9999 and b of degree 8999 with a gcd of degree 1000 (the largest
-    size of the paper's gcd timings, Section 6): deg g = 1000, deg u = 7999, deg w = 1000."""
-    return gcd_factors(1000, 7999, 1000, seed, p)
+    size of the paper's gcd timings, Section 6): a = g u, b = g v with deg u = 8999, deg v = 7999."""
+    return gcd_cofactors(1000, 8999, 7999, seed, p)

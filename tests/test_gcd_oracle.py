@@ -135,3 +135,13 @@ def test_special_cases():
     assert [int(v) for v in oracle.gcd(z, [0, 0, 3, 0], P)] == [0, 1]
     z[1] = 0
     assert [int(v) for v in oracle.gcd(z, [0, 0, 3, 0], P)] == [0, 0, 1]
+
+
+def test_workload_cofactors_are_coprime():
+    """The gcd workloads plant g through a = g u, b = g v: their gcd is g only if gcd(u, v) = 1."""
+    for seed_off, (dg, du, dv) in ((7, (1000, 8999, 7999)), (8, (200, 1799, 1299))):
+        g, u, v = inputs.gcd_cofactors(dg, du, dv, inputs.SEED_BASE + seed_off)
+        assert np.array_equal(oracle.gcd(u, v, P), [1])
+        assert int(g[-1]) == 1 and len(g) == dg + 1
+    g, u, v = inputs.workload_gcd()
+    assert np.array_equal(oracle.gcd(oracle.polymul(g, u, P), oracle.polymul(g, v, P), P), g)
