@@ -208,7 +208,7 @@ pm_status polymul_divide(const uint32_t *a, int64_t deg_a, const uint32_t *b, in
  *   p          prime, 2 <= p < PM_MAX_P (primality is not checked; a leading
  *              coefficient without an inverse sets PM_ERR_INVALID_ARG in the
  *              status word)
- *   s          division steps per launch, 1 <= s <= 256; 0 picks 128
+ *   s          division steps per launch, 1 <= s <= 256; 0 picks 64
  *   stream     cudaStream_t as void*
  * The number of division steps (at most deg_a + deg_b + 2) depends on the
  * data, so the call launches rounds of s steps in batches and reads a

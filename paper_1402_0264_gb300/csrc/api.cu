@@ -234,7 +234,7 @@ pm_status polymul_gcd(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64
     const int64_t ng = std::max(deg_a, deg_b) + 1;
     if (overlaps(g, ng, a, deg_a + 1) || overlaps(g, ng, b, deg_b + 1)) return PM_ERR_INVALID_ARG;
     if (is_capturing(stream)) return PM_ERR_UNSUPPORTED;  // the call reads its state back between rounds
-    if (s == 0) s = 128;
+    if (s == 0) s = 64;   // the fastest measured on GB300 (degrees 9999 and 8999)
     pm_status rc = PM_OK;
     DeviceWorkspace* ws = workspace(stream, &rc);
     if (!ws) return rc;

@@ -45,7 +45,7 @@
 
 namespace pm {
 
-constexpr int GCD_THREADS = 256;
+constexpr int GCD_THREADS = 512;                 // 16 warps: latency hiding for the replay
 constexpr int GCD_T = 256;                     // output positions per block
 constexpr int GCD_SMAX = 256;                  // largest s
 constexpr int GCD_HEXTRA = 32;                 // head length H = s + GCD_HEXTRA
@@ -130,12 +130,12 @@ __device__ __forceinline__ uint32_t gcd_strip(const uint32_t* h, int& u, int lim
 // One round.  X* are the arrays at the round's start, Y* receive the result;
 // sin/sout the state copies; ybuf names Y's copy for the final state.
 template <bool MONT>
-__global__ void __launch_bounds__(GCD_THREADS) gcd_round_kernel(
+__global__ void __launch_bounds__(GCD_THREADS, 1) gcd_round_kernel(
     const uint32_t* __restrict__ XA, const uint32_t* __restrict__ XB, uint32_t* __restrict__ YA,
     uint32_t* __restrict__ YB, const GcdState* __restrict__ sin, GcdState* __restrict__ sout, int s, int H,
     int ybuf, GcdMod md) {
     const uint32_t p = md.p;
-    __shared__ uint32_t hA[GCD_HMAX], hB[GCD_HMAX];
+    __shared__ uint32_t hAB[2 * GCD_HMAX];   // heads: a at [0, GCD_HMAX), b at [GCD_HMAX, 2 GCD_HMAX)
     __shared__ uint32_t rc1[GCD_SMAX], rc2[GCD_SMAX];
     __shared__ int rsig[GCD_SMAX];       // (shift << 1) | (1 when b is the reduced one)
     __shared__ uint32_t wA[GCD_WMAX], wB[GCD_WMAX];
@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(GCD_THREADS) gcd_round_kernel(
     } else {
         const int lane = tid;
         for (int j = lane; j < H; j += 32) {
-            hA[j] = da0 - j >= 0 ? XA[da0 - j] : 0u;
-            hB[j] = db0 - j >= 0 ? XB[db0 - j] : 0u;
+            hAB[j] = da0 - j >= 0 ? XA[da0 - j] : 0u;
+            hAB[GCD_HMAX + j] = db0 - j >= 0 ? XB[db0 - j] : 0u;
         }
         __syncwarp();
         // offsets (from the round's tops) of the leading coefficients and exact head lengths; the
@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(GCD_THREADS) gcd_round_kernel(
         // 32-bit integers
         const int Da = (int)da0, Db = (int)db0, D0 = Da - Db;
         int ua = 0, ub = 0, va = H, vb = H;
-        uint32_t la = gcd_strip(hA, ua, min(va, Da + 1), lane);
-        uint32_t lb = gcd_strip(hB, ub, min(vb, Db + 1), lane);
+        uint32_t la = gcd_strip(hAB, ua, min(va, Da + 1), lane);
+        uint32_t lb = gcd_strip(hAB + GCD_HMAX, ub, min(vb, Db + 1), lane);
         int k = 0, kind = -1;
         int64_t dg = -1;
         for (int guard = 0; guard < GCD_SMAX + 2; ++guard) {
@@ -187,59 +187,49 @@ __global__ void __launch_bounds__(GCD_THREADS) gcd_round_kernel(
             }
             if (ua == Da || ub == Db) { kind = GCD_IS_ONE; dg = 0; break; }   // a nonzero constant
             if (k == s) break;
-            const int sig = ub - ua;
-            if (ua - ub <= D0) {
-                // a <- lc(b) a - lc(a) x^(deg a - deg b) b on the head: a[ua+j] pairs with b[ub+j].
-                // Entries past what the remaining steps can reach (plus GCD_HEXTRA) are left stale
-                // and count as unknown: a round whose degrees drop that far ends early instead.
-                const uint32_t c1 = lb, c2n = p - la;
-                const int va_new = min(min(va, ua + vb - ub), ua + (s - k) + GCD_HEXTRA);
-                // the next 32 entries first: the new leading coefficient is the first nonzero one
-                const int i0h = ua + 1 + lane;
-                uint32_t v = 0u;
-                if (i0h < va_new) {
-                    v = gcd_comb<MONT>(c1, hA[i0h], c2n, hB[i0h + sig], md);
-                    hA[i0h] = v;
-                }
-                const unsigned msk = __ballot_sync(0xffffffffu, v != 0u);
-                const int f = __ffs(msk) - 1;
-                const uint32_t lnew = __shfl_sync(0xffffffffu, v, f < 0 ? 0 : f);
+            // One step in one code path: the reduced polynomial r (a when deg a >= deg b) loses its
+            // leading term to lc(d) r - lc(r) x^(deg r - deg d) d, d the other one; r[ur+j] pairs with
+            // d[ud+j].  Entries past what the remaining steps can reach (plus GCD_HEXTRA) are left
+            // stale and count as unknown: a round whose degrees drop that far ends early instead.
+            const bool redA = ua - ub <= D0;
+            const int offr = redA ? 0 : GCD_HMAX, offd = GCD_HMAX - offr;
+            const int ur = redA ? ua : ub, ud = redA ? ub : ua;
+            const int vr = redA ? va : vb, vd = redA ? vb : va;
+            const int Dr = redA ? Da : Db;
+            const uint32_t c1 = redA ? lb : la, c2n = p - (redA ? la : lb);
+            const int sh = ud - ur;
+            const int vr_new = min(min(vr, ur + vd - ud), ur + (s - k) + GCD_HEXTRA);
+            // the next 32 entries first: the new leading coefficient is the first nonzero one
+            const int i0h = ur + 1 + lane;
+            const bool live = i0h < vr_new;
+            uint32_t v = gcd_comb<MONT>(c1, hAB[offr + (live ? i0h : 0)], c2n, hAB[offd + (live ? i0h + sh : 0)], md);
+            v = live ? v : 0u;
+            if (live) hAB[offr + i0h] = v;
+            const unsigned msk = __ballot_sync(0xffffffffu, v != 0u);
+            const int f = __ffs(msk) - 1;
+            uint32_t lnew = __shfl_sync(0xffffffffu, v, f < 0 ? 0 : f);
 #pragma unroll 4
-                for (int i = i0h + 32; i < va_new; i += 32) hA[i] = gcd_comb<MONT>(c1, hA[i], c2n, hB[i + sig], md);
-                if (lane == 0) { rc1[k] = c1; rc2[k] = c2n; rsig[k] = sig * 2; }
-                va = va_new;
-                if (msk) {
-                    ua += 1 + f;
-                    la = lnew;
-                } else {   // 32 zeros: strip on from the entries the loop above wrote
-                    ua = min(ua + 33, min(va, Da + 1));
-                    __syncwarp();
-                    la = gcd_strip(hA, ua, min(va, Da + 1), lane);
-                }
+            for (int i = i0h + 32; i < vr_new; i += 32)
+                hAB[offr + i] = gcd_comb<MONT>(c1, hAB[offr + i], c2n, hAB[offd + i + sh], md);
+            if (lane == 0) {
+                rc1[k] = c1;
+                rc2[k] = c2n;
+                rsig[k] = (ub - ua) * 2 + (redA ? 0 : 1);
+            }
+            int ur_new = ur + 1 + f;
+            if (!msk) {   // 32 zeros: strip on from the entries the loop above wrote
+                ur_new = min(ur + 33, min(vr_new, Dr + 1));
+                __syncwarp();
+                lnew = gcd_strip(hAB + offr, ur_new, min(vr_new, Dr + 1), lane);
+            }
+            if (redA) {
+                ua = ur_new;
+                va = vr_new;
+                la = lnew;
             } else {
-                const uint32_t c1 = la, c2n = p - lb;
-                const int vb_new = min(min(vb, ub + va - ua), ub + (s - k) + GCD_HEXTRA);
-                const int i0h = ub + 1 + lane;
-                uint32_t v = 0u;
-                if (i0h < vb_new) {
-                    v = gcd_comb<MONT>(c1, hB[i0h], c2n, hA[i0h - sig], md);
-                    hB[i0h] = v;
-                }
-                const unsigned msk = __ballot_sync(0xffffffffu, v != 0u);
-                const int f = __ffs(msk) - 1;
-                const uint32_t lnew = __shfl_sync(0xffffffffu, v, f < 0 ? 0 : f);
-#pragma unroll 4
-                for (int i = i0h + 32; i < vb_new; i += 32) hB[i] = gcd_comb<MONT>(c1, hB[i], c2n, hA[i - sig], md);
-                if (lane == 0) { rc1[k] = c1; rc2[k] = c2n; rsig[k] = sig * 2 + 1; }
-                vb = vb_new;
-                if (msk) {
-                    ub += 1 + f;
-                    lb = lnew;
-                } else {
-                    ub = min(ub + 33, min(vb, Db + 1));
-                    __syncwarp();
-                    lb = gcd_strip(hB, ub, min(vb, Db + 1), lane);
-                }
+                ub = ur_new;
+                vb = vr_new;
+                lb = lnew;
             }
             ++k;
             __syncwarp();
