@@ -178,6 +178,25 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def division_model_ratio(n: int, m: int, s: int, ell: int, U: float) -> float:
+    """T_1 / T_s of Section 3 (Corollary 1 with K_1 = m / l, K_s = m / (2 s)): the naive division
+    (N_1 / K_1 = n - m + 1, L_1 = n - m + 1, C_1 = 3 + 5U) over the optimized one
+    (N_s = (n - m + 1) m / (2 s^2), L_s = (n - m + 1) / s, C_s = 3 s + 9 U); a has n terms, b m."""
+    mu = n - m + 1
+    t1 = (mu * m / ell / (m / ell) + mu) * (3 + 5 * U)
+    ts = (mu * m / (2 * s * s) / (m / (2 * s)) + mu / s) * (3 * s + 9 * U)
+    return t1 / ts
+
+
+def gcd_model_ratio(n: int, m: int, s: int, ell: int, U: float) -> float:
+    """T_1 / T_s of Section 6 (Corollary 1 with K_1 = m / l, K_s = m / s): the naive gcd
+    (N_1 = m (n + l + 1) / l, L_1 = n + m - 2, C_1 = 3 + 5U) over the optimized one
+    (N_s = m n / s^2 + m / s, L_s = (n + m) / s, C_s = 3 s + 8 U); a has n terms, b m."""
+    t1 = (m * (n + ell + 1) / ell / (m / ell) + n + m - 2) * (3 + 5 * U)
+    ts = ((m * n / (s * s) + m / s) / (m / s) + (n + m) / s) * (3 * s + 8 * U)
+    return t1 / ts
+
+
 def eval_mod(poly, r: int, p: int) -> int:
     """poly(r) mod p on the host with numpy (a spot check of a product: c(r) = a(r) b(r) mod p
     for a product c = a b, the Schwartz-Zippel test).  Powers r^i as r^(i mod B) (r^B)^(i div B)."""
@@ -587,16 +606,13 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
         assert pm.sync_status() == 0 and division_holds(t1a, t1b, q1, r1), f"division s={s_d}: a != q b + r"
         small[s_d] = median_ms(lambda s_d=s_d: pm.divide(t1a, t1b, s=s_d, q=q1, r=r1), 3, flush, stream)
     U = 4.0 * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6 * SMS / (pk["hbm_gbs"] * 1e9)
-    mu_, m_ = len(a1) - len(b1) + 1, len(b1)
-    ell1, s_ = 256, 256
-    T1 = (mu_ * m_ / ell1 / (m_ / ell1) + mu_) * (3 + 5 * U)
-    Ts = (mu_ * m_ / (2 * s_ * s_) / (m_ / (2 * s_)) + mu_ / s_) * (3 * s_ + 9 * U)
+    div_ratio = division_model_ratio(len(a1), len(b1), 256, 256, U)
     rows["division"] = {"workload": "a of degree 32767 divided by b of degree 16383",
                         "work_macs": work_d, "s_sweep": sweep,
                         "best_s": min(sweep, key=lambda e: e["ms"])["s"],
                         "naive_vs_s256_deg4095_by_2047": {"ms_s1": small[1], "ms_s256": small[256],
                                                          "measured_ratio": small[1] / small[256],
-                                                         "model_ratio_T1_over_Ts": T1 / Ts, "U": U}}
+                                                         "model_ratio_T1_over_Ts": div_ratio, "U": U}}
 
     # --- gcd (Section 6, Algorithms 10-11): a of degree 9999, b of degree 8999, planted gcd of degree 1000 ---
     def planted_on_gpu(g_np, u_np, v_np):
@@ -617,8 +633,6 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
         sweep.append({"s": s_g, "ms": ms, "us_per_step": ms * 1e3 / steps_g})
     # s = 1 (the naive gcd of Algorithms 8-9, one step per launch) against s = 256 on the smallest size of
     # the paper's gcd timings (degrees 1999 and 1499), with the running-time ratio T_1 / T_s of Corollary 1
-    # and the costs of Section 6 (N_1 / K_1 = n + l + 1, L_1 = n + m - 2, C_1 = 3 + 5U;
-    # N_s / K_s = n / s + 1, L_s = (n + m) / s, C_s = 3 s + 8 U)
     g1, u1, v1 = inputs.gcd_cofactors(200, 1799, 1299, inputs.SEED_BASE + 8)
     sa, sb, sg = planted_on_gpu(g1, u1, v1)
     sout = torch.empty(max(sa.numel(), sb.numel()), dtype=torch.uint32, device=dev)
@@ -627,15 +641,13 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
         res = pm.gcd(sa, sb, s=s_g, out=sout)
         assert pm.sync_status() == 0 and torch.equal(res, sg), f"gcd s={s_g}: not the planted gcd"
         small[s_g] = median_ms(lambda s_g=s_g: pm.gcd(sa, sb, s=s_g, out=sout), 3, flush, stream)
-    n_g, m_g, ell_g, s_m = sa.numel(), sb.numel(), 256, 256
-    T1g = (n_g + ell_g + 1 + n_g + m_g - 2) * (3 + 5 * U)
-    Tsg = (n_g / s_m + 1 + (n_g + m_g) / s_m) * (3 * s_m + 8 * U)
+    gcd_ratio = gcd_model_ratio(sa.numel(), sb.numel(), 256, 256, U)
     rows["gcd"] = {"workload": "a of degree 9999, b of degree 8999, planted gcd of degree 1000",
                    "division_steps": steps_g, "s_sweep": sweep,
                    "best_s": min(sweep, key=lambda e: e["ms"])["s"],
                    "naive_vs_s256_deg1999_and_1499": {"ms_s1": small[1], "ms_s256": small[256],
                                                       "measured_ratio": small[1] / small[256],
-                                                      "model_ratio_T1_over_Ts": T1g / Tsg, "U": U}}
+                                                      "model_ratio_T1_over_Ts": gcd_ratio, "U": U}}
     return rows
 
 
