@@ -45,7 +45,7 @@
 
 namespace pm {
 
-constexpr int GCD_THREADS = 512;                 // 16 warps: latency hiding for the replay
+constexpr int GCD_THREADS = 512;               // 16 warps: latency hiding for the replay
 constexpr int GCD_T = 256;                     // output positions per block
 constexpr int GCD_SMAX = 256;                  // largest s
 constexpr int GCD_HEXTRA = 32;                 // head length H = s + GCD_HEXTRA
