@@ -140,3 +140,24 @@ def test_gcd_validation_happens_on_host(lib):
     assert f(FAKE, 5, FAKE2, 3, G, dp, P, -1, NULL) == 1        # negative s
     assert f(FAKE, 5, FAKE2, 3, FAKE, dp, P, 0, NULL) == 1      # g overlapping a
     assert f(FAKE, 5, FAKE2, 3, FAKE2, dp, P, 0, NULL) == 1     # g overlapping b
+
+
+def test_binding_refuses_host_tensors(lib):
+    """The product path has no CPU fallback: every entry point of the binding refuses host tensors
+    before anything reaches the library."""
+    import torch
+    a = torch.ones(16, dtype=torch.uint32)
+    b = torch.ones(9, dtype=torch.uint32)
+    off = torch.tensor([0, 16], dtype=torch.int64)
+    calls = [
+        lambda: pm.plain(a, b),
+        lambda: pm.plain_ell(a, b, 8, 128),
+        lambda: pm.plain_noalloc(a, b),
+        lambda: pm.ntt(a, b),
+        lambda: pm.divide(a, b),
+        lambda: pm.gcd(a, b),
+        lambda: pm.batched(a, off, a, off, torch.tensor([0, 31], dtype=torch.int64), max_deg=15),
+    ]
+    for call in calls:
+        with pytest.raises(TypeError):
+            call()
