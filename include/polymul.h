@@ -71,7 +71,9 @@ typedef enum {
  *   s          per-thread block parameter: 1, 2, 4, 8, 16, 32 or 64; 0 picks
  *              the tuned value for this size (polymul_tune_plain) or a default
  *   stream     cudaStream_t as void*
- * Returns PM_OK, PM_ERR_INVALID_ARG or PM_ERR_CUDA.
+ * Returns PM_OK, PM_ERR_INVALID_ARG (pointers, degrees, s, c overlapping an
+ * input), PM_ERR_RANGE (p), PM_ERR_UNSUPPORTED (scratch growth while the
+ * stream captures), PM_ERR_NOMEM or PM_ERR_CUDA.
  */
 pm_status polymul_plain(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
                         uint32_t *c, uint32_t p, int s, void *stream);
@@ -85,7 +87,10 @@ pm_status polymul_plain(const uint32_t *a, int64_t deg_a, const uint32_t *b, int
  *   ell        128, 256 (polymul_plain's block) or 512
  *   s          1, 2, 4, 8, 16, 32 or 64 (no tuned default)
  *   other arguments as for polymul_plain.
- * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_RANGE or PM_ERR_CUDA.
+ * At ell = 512 a thread may hold 128 registers, and s = 64 then keeps its
+ * window of a in local memory (exact, but about 19x slower than ell = 256).
+ * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_RANGE, PM_ERR_UNSUPPORTED,
+ * PM_ERR_NOMEM or PM_ERR_CUDA.
  */
 pm_status polymul_plain_ell(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
                             uint32_t *c, uint32_t p, int s, int ell, void *stream);
