@@ -27,7 +27,10 @@
  *     one uncaptured call of the same shape first.
  *   - Thread safety: calls from several host threads are allowed; workspace
  *     growth is serialised by a lock.  Calls that share a device and run
- *     concurrently on different streams must not share output buffers.
+ *     concurrently on different streams must not share output buffers.  A
+ *     call's launches use its stream's scratch, so two host threads must not
+ *     issue calls on the same stream at the same time (their launches could
+ *     interleave); give each thread its own stream.
  */
 #ifndef POLYMUL_H
 #define POLYMUL_H
