@@ -1,25 +1,28 @@
 #!/usr/bin/env python3
 """Benchmark: modular coefficient MACs/s of dense polynomial multiplication
 mod p = 469762049 on one GB300.  Parity with the CPU oracle is the tests'
-job; here the oracle runs only in the cpu_baseline leg (which also compares
-its product with the GPU's headline result word for word) and in the
-reference arm, and every other result is cross-checked on the GPU (plain
-against transform, tensor-core against plain, graph against direct, a
-division against a = q b + r, a gcd against its planted factor, a transform
-product at a random point).
+job; here the oracle runs only in the cpu_baseline legs (which also compare
+their products with the GPU's results word for word) and in the reference
+arm, and every other result is cross-checked on the GPU (tensor-core against
+plain, plain against transform, graph against direct, a division against
+a = q b + r, a gcd against its planted factor, a transform product at a
+random point).
 
-Headline step: one product of a degree-16383 pair (n = m = 16384, so
-n*m = 2^28 modular multiply-adds) by the s-blocked plain kernel at the tuned
-s.  Each timed step is bracketed by CUDA events on the launching stream and
-preceded by a 256 MiB write that flushes the 129 MB L2 (outside the events).
+Headline step: the batched tensor-core product of 1024 pairs of degree 4095
+(1024 * 4096^2 = 1.72e10 modular multiply-adds), one polymul_batched call
+with PM_TENSOR (a planning launch and one persistent tcgen05 kernel).  Each
+timed step is bracketed by CUDA events on the launching stream and preceded
+by a 256 MiB write that flushes the 129 MB L2 (outside the events).  The
+roofline is the tensor one: 20 bf16 limb products per modular MAC (2 flops
+each) over the measured bf16 peak.  The one-pair degree-16383 product of
+the s-blocked plain kernel (the paper's Section 5 form) is the row
+`plain_single`, with its own ALU roofline, e2e and CPU baseline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-rows]
 
 Prints one JSON line.  With N > 1 (torchrun) every rank runs its own replica
-of the step (the product does not shard here) and rank 0 reports the job
-total over the slowest rank's time.  `rows` holds the other measured paths:
-the s sweep with the cost model's predictions, the batched form, and (where
-built) the tensor-core and transform forms.
+of the step (the work is not sharded here) and rank 0 reports the job total
+over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -44,13 +47,43 @@ from paper_1402_0264_gb300 import inputs  # noqa: E402
 P = inputs.P_DEFAULT
 METRIC = "modular coefficient MACs/s (n*m per product), bit-exact vs oracle"
 UNIT = "MAC/s"
+BATCH_T, DEG_T = 1024, 4095
+MACS_T = BATCH_T * (DEG_T + 1) ** 2        # 1.718e10 modular multiply-adds per step
+LIMB_PRODUCTS = 20                          # 5 balanced base-64 limbs of a x 4 base-256 limbs of b
+FLOPS_PER_MAC = 2 * LIMB_PRODUCTS           # bf16 flops of useful tensor work per modular MAC
+WORKLOAD = ("batched tensor-core polymul mod p=469762049: 1024 pairs of degree 4095, uint32 coefficients "
+            "uniform in [0,p), bf16 limbs on tcgen05 with exact fp32 accumulation and a fused mod-p epilogue")
 N_SINGLE = 16384
 MACS_SINGLE = N_SINGLE * N_SINGLE
-WORKLOAD = "plain polymul mod p=469762049, one pair of degree 16383, uint32 coefficients uniform in [0,p)"
+WORKLOAD_SINGLE = "plain polymul mod p=469762049, one pair of degree 16383, uint32 coefficients uniform in [0,p)"
 FLUSH_BYTES = 256 << 20
 SMS = 152
-IMAD_PER_CLK_SM = 32      # acc64 += u32*u32 (IMAD.WIDE.U32) issue rate measured on GB300: one per modular MAC
+IMAD_PER_CLK_SM = 32      # nominal 32x32->64 multiply-add issue rate (half the 32-bit IMAD rate); the bench measures it
 SM_MAX_MHZ = 2070.0
+L2_NOTE = "flushed between steps (256 MiB write outside the timed events)"
+
+
+def headline_config(world: int) -> dict:
+    return {"workload": WORKLOAD, "batch": BATCH_T, "deg": DEG_T, "p": P, "mode": "PM_TENSOR",
+            "parallelism": "replicas" if world > 1 else "single", "l2": L2_NOTE}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def peaks():
@@ -63,9 +96,9 @@ def peaks():
                 "sm_max_mhz": SM_MAX_MHZ}, "fallback"
 
 
-def alu_peak_macs(mhz=SM_MAX_MHZ):
-    """Plain-path ceiling: one mad.wide.u32 per modular MAC, 64 per SM per clock."""
-    return SMS * IMAD_PER_CLK_SM * mhz * 1e6
+def alu_peak_macs(rate=IMAD_PER_CLK_SM, mhz=SM_MAX_MHZ):
+    """Plain-path ceiling: one 32x32->64 multiply-add per modular MAC, `rate` per SM per clock."""
+    return SMS * rate * mhz * 1e6
 
 
 def source_hash(*names):
@@ -222,37 +255,41 @@ def eval_mod(poly, r: int, p: int) -> int:
 # ---------------------------------------------------------------------------
 
 def run_reference(args, world, rank):
-    """The oracle on the host cores.  Each step is the full product when K+W full
-    products fit in about two minutes, else the product of the leading n' terms
-    of both operands (a bounded sample of the same workload, n'^2 MACs)."""
+    """The oracle on the host cores: the 1024 pairs of degree 4095 by the long-multiplication
+    definition, the pairs shared out over all host threads (OpenMP).  Each step is the whole
+    batch when K+W of them fit in about two minutes, else the first `pairs` pairs of it (a
+    bounded sample of the same workload; the MAC count is that of the pairs done)."""
     if rank != 0:
         return 0
     import oracle
-    a, b = inputs.workload_single()
+    tp = inputs.workload_tensor()
+    a_data, a_off, b_data, b_off, c_off = tp
+    threads = oracle.omp_threads()
     t0 = time.perf_counter()
-    oracle.polymul(a, b, P)  # build, load and time one full product
-    t_full = time.perf_counter() - t0
+    oracle.polymul_batch_omp(a_data, a_off[:9], b_data, b_off[:9], c_off[:9], P)  # build, load, time 8 pairs
+    t8 = time.perf_counter() - t0
     budget = 120.0 / max(1, args.steps + args.warmup)
-    nn = N_SINGLE
-    if t_full > budget:
-        nn = max(256, int(N_SINGLE * math.sqrt(budget / t_full)))
-    a_s, b_s = a[:nn], b[:nn]
+    pairs = BATCH_T if t8 / 8 * BATCH_T <= budget else max(threads, int(budget / (t8 / 8)) // threads * threads)
+    pairs = min(pairs, BATCH_T)
+    sub = (a_data, a_off[:pairs + 1], b_data, b_off[:pairs + 1], c_off[:pairs + 1])
     for _ in range(args.warmup):
-        oracle.polymul(a_s, b_s, P)
+        oracle.polymul_batch_omp(*sub, P)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.polymul(a_s, b_s, P)
+        oracle.polymul_batch_omp(*sub, P)
     dt = time.perf_counter() - t0
-    value = nn * nn * args.steps / dt
-    sample = (f"{args.steps} full products of the degree-16383 pair" if nn == N_SINGLE else
-              f"{args.steps} products of the leading {nn} terms of both operands of the degree-16383 pair")
+    macs = pairs * (DEG_T + 1) ** 2
+    value = macs * args.steps / dt
+    sample = (f"{args.steps} runs of the whole batch" if pairs == BATCH_T else
+              f"{args.steps} runs of the first {pairs} of the 1024 pairs")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N_SINGLE, "m": N_SINGLE, "p": P},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample + " (single-thread C schoolbook, 128-bit accumulation)"},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": headline_config(world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "cpu": cpu_model(),
+                             "sample": sample + " (C schoolbook with 128-bit accumulation, pairs over "
+                                                f"{threads} OpenMP threads)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -261,6 +298,34 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+
+TC_CHUNK_BLOCKS = 48  # output blocks of 32 per MMA column chunk of the tensor kernel (5 columns each)
+
+
+def tc_issued_flops(a_off, b_off) -> float:
+    """bf16 flops the tensor kernel issues for a batch (padding included): per tile of 1536
+    outputs (48 blocks) and per shift it meets, 2 MMAs of 128 x N x 16, N = 5 columns per block
+    over the chunks of TC_CHUNK_BLOCKS blocks that hold a nonzero block."""
+    n_all = np.diff(a_off)
+    m_all = np.diff(b_off)
+    tot = 0
+    for n_, m_ in zip(n_all.tolist(), m_all.tolist()):
+        if m_ > n_:
+            n_, m_ = m_, n_
+        na = (n_ + 31) // 32
+        dmax = (m_ + 30) // 32
+        nblk = (n_ + m_ - 1 + 31) // 32
+        for t_ in range((n_ + m_ - 1 + 1535) // 1536):
+            I0 = 48 * t_
+            for d in range(max(0, I0 - na + 1), min(dmax, I0 + 47) + 1):
+                lo = max(I0, d)                      # first block of the tile this shift meets
+                hi = min(I0 + 47, d + na - 1, nblk - 1)  # last one
+                if hi < lo:
+                    continue
+                c0, c1 = (lo - I0) // TC_CHUNK_BLOCKS, (hi - I0) // TC_CHUNK_BLOCKS
+                tot += (c1 - c0 + 1) * 5 * TC_CHUNK_BLOCKS
+    return float(tot) * 2 * 2 * 128 * 16
+
 
 def run_ours(args, world, rank, local):
     import torch
@@ -278,24 +343,22 @@ def run_ours(args, world, rank, local):
     def flush():
         flush_buf.zero_()
 
-    a_np, b_np = inputs.workload_single()
-    a = torch.from_numpy(a_np).to(dev)
-    b = torch.from_numpy(b_np).to(dev)
-    c = torch.empty(2 * N_SINGLE - 1, dtype=torch.uint32, device=dev)
+    tp = inputs.workload_tensor()
+    tt = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in tp]
+    total = int(tp[4][-1])
+    out = torch.empty(total, dtype=torch.uint32, device=dev)
 
-    # autotune s on this size (the tuner records it; s = 0 calls then use it)
-    if args.s:
-        s, tune_ms = args.s, {}
-    else:
-        s, tune_ms = pm.tune_plain(a, b, reps=10, out=c)
+    def step():
+        pm.batched(tt[0], tt[1], tt[2], tt[3], tt[4], max_deg=DEG_T, mode=pm.PM_TENSOR, out=out, total=total)
 
-    # warm-up; the warmed result agrees with the transform path (the oracle itself runs in the
-    # cpu_baseline leg below, which also checks this result word for word)
+    # warm-up; the warmed result agrees with the plain CUDA-core form on the same batch (the oracle
+    # itself runs in the cpu_baseline leg below, which also checks this result word for word)
     for _ in range(args.warmup):
-        pm.plain(a, b, s=s, out=c)
-    cross = pm.ntt(a, b)
+        step()
+    plain_out = pm.batched(tt[0], tt[1], tt[2], tt[3], tt[4], max_deg=DEG_T, mode=pm.PM_PLAIN, s=8, total=total)
     torch.cuda.synchronize()
-    assert torch.equal(c, cross), "bench: the plain and transform paths disagree"
+    assert torch.equal(out, plain_out), "bench: the tensor-core and plain forms disagree"
+    del plain_out
     assert pm.sync_status() == 0
 
     K = args.steps
@@ -314,7 +377,7 @@ def run_ours(args, world, rank, local):
         for i in range(K):
             flush()
             starts[i].record(stream)
-            pm.plain(a, b, s=s, out=c)
+            step()
             ends[i].record(stream)
         torch.cuda.synchronize()
         barrier(world)
@@ -323,13 +386,15 @@ def run_ours(args, world, rank, local):
     clocks = sampler.summary()
     step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
     total_ms = max_over_ranks(sum(step_ms), world)
-    value = world * MACS_SINGLE * K / (total_ms * 1e-3)
+    value = world * MACS_T * K / (total_ms * 1e-3)
     ms_per_step = total_ms / K
+    assert pm.sync_status() == 0
 
-    # end to end through the C ABI from pinned host buffers (H2D, product, D2H each step)
-    a_h = torch.from_numpy(a_np).pin_memory()
-    b_h = torch.from_numpy(b_np).pin_memory()
-    c_h = torch.empty(2 * N_SINGLE - 1, dtype=torch.uint32).pin_memory()
+    # end to end through the C ABI from pinned host buffers: every step copies its inputs (both
+    # coefficient arrays and the three offset arrays) in, runs the product and copies the 1024
+    # products out, all inside the events
+    hosts = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in tp]
+    out_h = torch.empty(total, dtype=torch.uint32).pin_memory()
     e_starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     e_ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     barrier(world)
@@ -337,51 +402,54 @@ def run_ours(args, world, rank, local):
     for i in range(K):
         flush()
         e_starts[i].record(stream)
-        a.copy_(a_h, non_blocking=True)
-        b.copy_(b_h, non_blocking=True)
-        pm.plain(a, b, s=s, out=c)
-        c_h.copy_(c, non_blocking=True)
+        for d_, h_ in zip(tt, hosts):
+            d_.copy_(h_, non_blocking=True)
+        step()
+        out_h.copy_(out, non_blocking=True)
         e_ends[i].record(stream)
     torch.cuda.synchronize()
     barrier(world)
     e2e_ms = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in zip(e_starts, e_ends)), world)
-    assert np.array_equal(c_h.numpy(), c.cpu().numpy()), "bench: the host copy differs from the device result"
+    gpu_result = out_h.numpy().view(np.uint32).copy()
+    assert np.array_equal(gpu_result, out.cpu().numpy().view(np.uint32)), \
+        "bench: the host copy differs from the device result"
 
     if rank != 0:
         return 0
 
     pk, pk_kind = peaks()
-    kern_name = f"plain_sk_kernel<{s}>"
-    achieved = MACS_SINGLE / (ms_per_step * 1e-3)
-    peak = alu_peak_macs()
+    achieved = MACS_T * FLOPS_PER_MAC / (ms_per_step * 1e-3) / 1e12
+    issued = tc_issued_flops(tp[1], tp[3]) / (ms_per_step * 1e-3) / 1e12
+    peak = pk["bf16_tflops"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "products_per_s": value / MACS_SINGLE,
-        "config": {"workload": WORKLOAD, "n": N_SINGLE, "m": N_SINGLE, "p": P, "s": s,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between steps (256 MiB write outside the timed events)"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "MAC/s",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "products_per_s": value / MACS_T * BATCH_T,
+        "config": headline_config(world),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "peak_basis": "152 SMs x 32 IMAD.WIDE.U32 (64-bit accumulate) per clk per SM, measured, x 2070 MHz max SM clock; one per modular MAC",
-                     "frac_at_sampled_clock": (achieved / alu_peak_macs(clocks["sm_mhz"])
-                                               if clocks.get("sm_mhz") else None),
-                     "kernel": kern_name,
-                     "traffic": traffic_for(f"plain_sk_kernel<{s}>", "plain.cu", "common.cuh")},
-        "e2e": {"value": world * MACS_SINGLE * K / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": int(a_h.numel() * 4 + b_h.numel() * 4),
-                "d2h_bytes_per_step": int(c_h.numel() * 4)},
+                     "peak_basis": f"measured bf16 dense GEMM, burst ({pk_kind}): the step is one short "
+                                   "kernel timed alone",
+                     "achieved_basis": "useful work only: 20 bf16 limb products (40 flops) per modular MAC, "
+                                       "n*m MACs per pair, no tile padding; over the CUDA-event time of the "
+                                       "whole call (planning launch included)",
+                     "issued_tflops": issued, "issued_frac": issued / peak,
+                     "kernel": "tc_batched_kernel",
+                     "traffic": traffic_for("tc_batched_kernel", "tensor.cu", "common.cuh")},
+        "e2e": {"value": world * MACS_T * K / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(h_.numel() * h_.element_size() for h_ in hosts)),
+                "d2h_bytes_per_step": int(out_h.numel() * 4)},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "wall_s_timed_region": wall,
         "peaks_source": pk_kind,
-        "tune_ms": {str(k): v for k, v in tune_ms.items()},
     }
     if world == 1 and not args.no_rows:
-        line["rows"] = measure_rows(pm, torch, dev, flush, clocks, pk)
+        line["rows"] = measure_rows(pm, torch, dev, flush, clocks, pk, args)
+        line["vs_plain_same_batch"] = line["rows"]["tensor_vs_plain"]
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a_np, b_np, c.cpu().numpy().view(np.uint32))
+        line["cpu_baseline"] = cpu_baseline_batch(tp, gpu_result)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -401,10 +469,21 @@ def median_ms(fn, reps, flush, stream):
     return statistics.median(ts)
 
 
-def measure_rows(pm, torch, dev, flush, clocks, pk):
+def measure_rows(pm, torch, dev, flush, clocks, pk, args):
     stream = torch.cuda.current_stream()
     rows = {}
     mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+
+    # --- the ceiling of the plain path, measured: 32x32->64 multiply-adds per clock per SM ---
+    rate = pm.probe_mac_rate(threads=256, blocks_per_sm=4, iters=20000)
+    alu_peak = alu_peak_macs(rate, pk.get("sm_max_mhz") or SM_MAX_MHZ)
+    rows["alu_probe"] = {"imad_wide_per_clk_per_sm": rate, "sms": SMS,
+                         "sm_max_mhz": pk.get("sm_max_mhz") or SM_MAX_MHZ, "peak_macs_per_s": alu_peak,
+                         "how": "polymul_probe_mac_rate: 4 x 152 blocks of 256 threads, 16 independent "
+                                "64-bit sums per thread, per-SM cycle counters around the loops"}
+
+    # --- the one-pair degree-16383 product of the s-blocked kernel (Section 5), tuned s ---
+    rows["plain_single"] = plain_single_row(pm, torch, dev, flush, stream, alu_peak, rate, pk, args)
 
     # --- s sweep on the degree-16383 pair with the cost model beside each point ---
     a_np, b_np = inputs.workload_single()
@@ -413,15 +492,16 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
     c = torch.empty(2 * N_SINGLE - 1, dtype=torch.uint32, device=dev)
     ell = 256
     # U: time to move one 4-byte word per SM (HBM share) over the time of one
-    # local multiply-add, both per SM: (ops/clk/SM * 4 B * clk * SMs) / (HBM bytes/s)
-    U = 4.0 * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6 * SMS / (pk["hbm_gbs"] * 1e9)
-    unit_s = ell / (IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6)         # one local op of a whole block
+    # local multiply-add, both per SM: (ops/clk/SM * 4 B * clk * SMs) / (HBM bytes/s),
+    # with the multiply-add rate measured by the probe above
+    U = 4.0 * rate * SM_MAX_MHZ * 1e6 * SMS / (pk["hbm_gbs"] * 1e9)
+    unit_s = ell / (rate * SM_MAX_MHZ * 1e6)         # one local op of a whole block
     sweep = []
     for s in pm.S_CANDIDATES:
         ms = median_ms(lambda: pm.plain(a, b, s=s, out=c), 20, flush, stream)
         pred = pm.model_predict(N_SINGLE, N_SINGLE, s, ell, U, float(SMS))
         sweep.append({"s": s, "ms": ms, "macs_per_s": MACS_SINGLE / (ms * 1e-3),
-                      "alu_frac": MACS_SINGLE / (ms * 1e-3) / alu_peak_macs(),
+                      "alu_frac": MACS_SINGLE / (ms * 1e-3) / alu_peak,
                       "model_T_thm_s": pred["T_thm"] * unit_s, "model_T_cor_s": pred["T_cor"] * unit_s,
                       "model_W": pred["W"], "model_O": pred["O"]})
     rows["plain_s_sweep"] = {"workload": "degree-16383 pair", "ell": ell, "U": U, "P": SMS,
@@ -435,7 +515,7 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
                        "model_T_cor_s": r["model_T_cor_s"]} for r in sweep]}
     ref = c.clone()
     for el in (128, 512):
-        u_el = el / (IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6)
+        u_el = el / (rate * SM_MAX_MHZ * 1e6)
         pts = []
         for s in pm.S_CANDIDATES:
             ms = median_ms(lambda: pm.plain_ell(a, b, s, el, out=c), 20, flush, stream)
@@ -498,9 +578,9 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
                              "tensor_form_ms_same_batch": ms_bt,
                              "macs": macs, "ms_graph": ms_g, "ms_direct": best[1],
                              "macs_per_s": macs / (ms_g * 1e-3), "products_per_s": 4096 / (ms_g * 1e-3),
-                             "alu_frac": macs / (ms_g * 1e-3) / alu_peak_macs()}
+                             "alu_frac": macs / (ms_g * 1e-3) / alu_peak}
 
-    # --- tensor-core form: 1024 pairs of degree 4095 (and the plain form on the same batch) ---
+    # --- the headline batch through the plain CUDA-core form (the comparison the tensor form must win) ---
     tp = inputs.workload_tensor()
     macs_t = int(((tp[1][1:] - tp[1][:-1]) * (tp[3][1:] - tp[3][:-1])).sum())
     tt = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in tp]
@@ -515,29 +595,12 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
     run_tp()
     ms_tp = median_ms(run_tp, 5, flush, stream)
     assert torch.equal(outt, want_t), "tensor and plain forms disagree on the 1024-pair batch"
-    # tensor work actually issued: per tile (1536 outputs) and shift, 2 MMAs of 128 x 240 x 16
-    tflops_issued = None
-    try:
-        nt = 0
-        for i in range(len(tp[1]) - 1):
-            n_ = int(tp[1][i + 1] - tp[1][i]); m_ = int(tp[3][i + 1] - tp[3][i])
-            if m_ > n_:
-                n_, m_ = m_, n_
-            NA = (n_ + 31) // 32; dmax = (m_ + 30) // 32
-            for t_ in range((n_ + m_ - 1 + 1535) // 1536):
-                I0 = 48 * t_
-                nt += min(dmax, I0 + 47) - max(0, I0 - NA + 1) + 1
-        tflops_issued = nt * 2 * 2 * 128 * 240 * 16 / (ms_t * 1e-3) / 1e12
-    except Exception:
-        pass
-    rows["tensor_batched"] = {"workload": "1024 pairs of degree 4095", "macs": macs_t, "ms": ms_t,
-                              "macs_per_s": macs_t / (ms_t * 1e-3), "products_per_s": 1024 / (ms_t * 1e-3),
-                              "plain_s8_ms_same_batch": ms_tp,
-                              "plain_s8_macs_per_s": macs_t / (ms_tp * 1e-3),
-                              "speedup_vs_plain": ms_tp / ms_t,
-                              "bf16_tflops_issued": tflops_issued,
-                              "tensor_frac_of_measured_bf16": (tflops_issued / pk["bf16_tflops"]
-                                                               if tflops_issued else None)}
+    rows["tensor_vs_plain"] = {"workload": "1024 pairs of degree 4095", "macs": macs_t, "tensor_ms": ms_t,
+                               "tensor_macs_per_s": macs_t / (ms_t * 1e-3), "plain_s8_ms": ms_tp,
+                               "plain_s8_macs_per_s": macs_t / (ms_tp * 1e-3),
+                               "plain_s8_alu_frac": macs_t / (ms_tp * 1e-3) / alu_peak,
+                               "speedup_tensor_over_plain": ms_tp / ms_t}
+    del tt, outt, want_t
 
     # --- transform path: one pair of degree 2^22 - 1, and the plain/transform crossover ---
     an, bn = inputs.workload_ntt()
@@ -605,7 +668,7 @@ def measure_rows(pm, torch, dev, flush, clocks, pk):
         pm.divide(t1a, t1b, s=s_d, q=q1, r=r1)
         assert pm.sync_status() == 0 and division_holds(t1a, t1b, q1, r1), f"division s={s_d}: a != q b + r"
         small[s_d] = median_ms(lambda s_d=s_d: pm.divide(t1a, t1b, s=s_d, q=q1, r=r1), 3, flush, stream)
-    U = 4.0 * IMAD_PER_CLK_SM * SM_MAX_MHZ * 1e6 * SMS / (pk["hbm_gbs"] * 1e9)
+    U = 4.0 * rate * SM_MAX_MHZ * 1e6 * SMS / (pk["hbm_gbs"] * 1e9)
     div_ratio = division_model_ratio(len(a1), len(b1), 256, 256, U)
     rows["division"] = {"workload": "a of degree 32767 divided by b of degree 16383",
                         "work_macs": work_d, "s_sweep": sweep,
@@ -741,9 +804,35 @@ def run_case(args):
     return 0
 
 
-def cpu_baseline(a_np, b_np, gpu_result):
-    """The oracle timed on one host core for about 10 s of full products; its product is also
-    compared word for word with the GPU's headline result."""
+def cpu_baseline_batch(tp, gpu_result):
+    """The oracle on all host cores (the pairs of the headline batch shared out over OpenMP
+    threads) for about 10 s of whole batches, plus one core on a sample of pairs; its products are
+    compared word for word with the GPU's."""
+    import oracle
+    a_data, a_off, b_data, b_off, c_off = tp
+    threads = oracle.omp_threads()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        want = oracle.polymul_batch_omp(a_data, a_off, b_data, b_off, c_off, P)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt > 10.0 or reps >= 50:
+            break
+    assert np.array_equal(gpu_result, want), "bench: the GPU's batch differs from the oracle"
+    k1 = 8  # one core: the first 8 pairs
+    t1 = time.perf_counter()
+    oracle.polymul_batch(a_data, a_off[:k1 + 1], b_data, b_off[:k1 + 1], c_off[:k1 + 1], P)
+    dt1 = time.perf_counter() - t1
+    return {"value": MACS_T * reps / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"{reps} runs of the whole 1024-pair batch ({dt:.1f} s), C schoolbook with 128-bit "
+                      f"accumulation, pairs over {threads} OpenMP threads",
+            "single_core_value": k1 * (DEG_T + 1) ** 2 / dt1,
+            "single_core_sample": f"the first {k1} pairs on one thread ({dt1:.2f} s)"}
+
+
+def cpu_baseline_single(a_np, b_np, gpu_result):
+    """The oracle on the degree-16383 pair: one thread for about 10 s of full products (its product is
+    compared word for word with the GPU's), then all host threads for about 5 s."""
     import oracle
     oracle.polymul(a_np[:8], b_np[:8], P)
     reps, t0 = 0, time.perf_counter()
@@ -754,15 +843,88 @@ def cpu_baseline(a_np, b_np, gpu_result):
         if dt > 10.0 or reps >= 100:
             break
     assert np.array_equal(gpu_result, want), "bench: the GPU result differs from the oracle"
-    return {"value": MACS_SINGLE * reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{reps} full products of the degree-16383 pair, single-thread C schoolbook "
-                      f"with 128-bit accumulation ({dt:.1f} s)"}
+    threads = oracle.omp_threads()
+    r2, t2 = 0, time.perf_counter()
+    while True:
+        oracle.polymul_omp(a_np, b_np, P)
+        r2 += 1
+        dt2 = time.perf_counter() - t2
+        if dt2 > 5.0 or r2 >= 1000:
+            break
+    return {"value": MACS_SINGLE * r2 / dt2, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"{r2} full products of the degree-16383 pair, coefficients over {threads} OpenMP "
+                      f"threads ({dt2:.1f} s)",
+            "single_core_value": MACS_SINGLE * reps / dt,
+            "single_core_sample": f"{reps} full products on one thread ({dt:.1f} s)"}
+
+
+def plain_single_row(pm, torch, dev, flush, stream, alu_peak, rate, pk, args):
+    """The one-pair degree-16383 product of the s-blocked kernel at the tuned s: per-step CUDA
+    events after an L2 flush, the ALU roofline, end to end from pinned host buffers, the oracle."""
+    a_np, b_np = inputs.workload_single()
+    a = torch.from_numpy(a_np).to(dev)
+    b = torch.from_numpy(b_np).to(dev)
+    c = torch.empty(2 * N_SINGLE - 1, dtype=torch.uint32, device=dev)
+    if args.s:
+        s, tune_ms = args.s, {}
+    else:  # flushed medians of 20 calls per s; near-ties go to the smaller s
+        s, tune_ms = pm.tune_plain(a, b, reps=20, out=c)
+    for _ in range(3):
+        pm.plain(a, b, s=s, out=c)
+    torch.cuda.synchronize()
+    assert torch.equal(c, pm.ntt(a, b)), "bench: the plain and transform paths disagree"
+    K = max(20, min(args.steps, 200))
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    l0 = pm.launch_count()
+    for i in range(K):
+        flush()
+        st[i].record(stream)
+        pm.plain(a, b, s=s, out=c)
+        en[i].record(stream)
+    torch.cuda.synchronize()
+    launches = pm.launch_count() - l0
+    ms = [x.elapsed_time(y) for x, y in zip(st, en)]
+    mean = sum(ms) / K
+    a_h = torch.from_numpy(a_np).pin_memory()
+    b_h = torch.from_numpy(b_np).pin_memory()
+    c_h = torch.empty(2 * N_SINGLE - 1, dtype=torch.uint32).pin_memory()
+    for i in range(K):
+        flush()
+        st[i].record(stream)
+        a.copy_(a_h, non_blocking=True)
+        b.copy_(b_h, non_blocking=True)
+        pm.plain(a, b, s=s, out=c)
+        c_h.copy_(c, non_blocking=True)
+        en[i].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = sum(x.elapsed_time(y) for x, y in zip(st, en)) / K
+    res = c_h.numpy().view(np.uint32).copy()
+    assert np.array_equal(res, c.cpu().numpy().view(np.uint32))
+    achieved = MACS_SINGLE / (mean * 1e-3)
+    mhz = pk.get("sm_max_mhz") or SM_MAX_MHZ
+    row = {"workload": WORKLOAD_SINGLE, "s": s, "steps": K, "ms_per_step": mean,
+           "ms_median": statistics.median(ms), "macs_per_s": achieved, "gpu_launches": int(launches),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "MAC/s",
+                        "frac": achieved / alu_peak,
+                        "peak_basis": f"measured in-tree: {rate:.2f} 32x32->64 multiply-adds per clk per SM "
+                                      f"(polymul_probe_mac_rate) x {SMS} SMs x {mhz:.0f} MHz max SM clock; "
+                                      "one per modular MAC",
+                        "kernel": f"plain_sk_kernel<{s}>",
+                        "traffic": traffic_for(f"plain_sk_kernel<{s}>", "plain.cu", "common.cuh")},
+           "e2e": {"value": MACS_SINGLE / (e2e_ms * 1e-3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(a_h.numel() * 4 + b_h.numel() * 4),
+                   "d2h_bytes_per_step": int(c_h.numel() * 4)},
+           "tune_ms": {str(k): v for k, v in tune_ms.items()}}
+    if not args.no_cpu_baseline:
+        row["cpu_baseline"] = cpu_baseline_single(a_np, b_np, res)
+    return row
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-rows", action="store_true")

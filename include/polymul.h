@@ -24,7 +24,12 @@
  *     tables, status word), grown on demand with cudaMalloc and freed by
  *     polymul_release().  A call that would have to grow it while `stream`
  *     is being captured into a CUDA graph returns PM_ERR_UNSUPPORTED: make
- *     one uncaptured call of the same shape first.
+ *     one uncaptured call of the same shape first.  A buffer replaced by a
+ *     larger one is kept (not freed) until polymul_release(), so a graph
+ *     captured before the growth stays valid.  Destroy every graph that holds
+ *     library calls before polymul_release(), and do not replay such a graph
+ *     while direct calls run on its capture stream's scratch (the same stream
+ *     the calls were captured on) from another stream.
  *   - Thread safety: calls from several host threads are allowed; workspace
  *     growth is serialised by a lock.  Calls that share a device and run
  *     concurrently on different streams must not share output buffers.  A
@@ -101,22 +106,25 @@ pm_status polymul_plain_ell(const uint32_t *a, int64_t deg_a, const uint32_t *b,
 /*
  * polymul_plain_noalloc - polymul_plain for callers that cannot allocate.
  * The paper has no counterpart: this is a deployment variant of the same
- * product.  Some callers cannot let a library call cudaMalloc: code that runs
- * while its stream is being captured into a CUDA graph (an allocation is not
- * a capturable operation), processes whose caching allocator has already
- * reserved nearly all device memory (a library's own cudaMalloc would fail),
- * and latency-bound callers that cannot take cudaMalloc's device-wide
- * synchronisation.  This entry point allocates nothing: the kernel's scratch
+ * product.  Some callers cannot let a library call cudaMalloc: processes whose
+ * caching allocator (PyTorch's, for one) has already reserved nearly all
+ * device memory, so that a library's own cudaMalloc would fail; latency-bound
+ * callers that cannot take the device-wide synchronisation that cudaMalloc and
+ * cudaFree may imply; and hosts whose memory policy gives every allocation to
+ * one owner.  This entry point allocates nothing: the kernel's scratch
  * (partial-sum slots and tile counters) lives in a 4 MiB static device array
  * that every GPU loading the library holds until the process exits.
  *
  *   Arguments, layout and result are those of polymul_plain.
  *   The first call on each device looks up the array's device address and
- *   clears its counters (synchronously); make that first call before any
- *   stream capture.  Later calls only launch the kernel.
- *   All calls share the one array (its contents persist between calls), so
- *   calls whose kernels overlap on the GPU - on different streams, or from
- *   different host threads - race and give wrong results: serialise them.
+ *   clears its counters (synchronously, on the legacy default stream); make
+ *   that first call before any stream capture (made while `stream` captures,
+ *   it returns PM_ERR_UNSUPPORTED and does nothing).  Later calls only launch
+ *   the kernel.
+ *   All calls share the one array (its contents persist between calls; the
+ *   kernel leaves its counters at zero), so calls whose kernels overlap on
+ *   the GPU - on different streams, or from different host threads - race and
+ *   give wrong results: serialise them.
  *   Returns PM_ERR_RANGE when the scratch a launch needs (2 slots of 32*s
  *   words per persistent CTA, plus the counters) would exceed the 4 MiB
  *   array; on GB300 every s fits.  Otherwise as polymul_plain.
@@ -247,13 +255,19 @@ pm_status polymul_model_predict(int64_t n, int64_t m, int s, int ell, double U, 
                                 double *out);
 
 /*
- * polymul_tune_plain - the autotuner: times polymul_plain for every s in
- * {1,2,4,8,16,32,64} (CUDA events, `reps` launches each after one warm-up)
- * on the caller's buffers, records the fastest s for this size class
- * (log2 buckets of n and m, and p below or above 2^29) so that later s = 0
- * calls use it, and returns the per-s milliseconds in times_ms[7]
- * (may be NULL) and the chosen s in *best_s.  Synchronises `stream`.
- * Returns what polymul_plain returns, or PM_ERR_CUDA.
+ * polymul_tune_plain - the autotuner of the block parameter s (the paper's
+ * strategy, Section 2.4 and Section 5: the s that the measured time favours
+ * among those the model allows).  For every s in {1,2,4,8,16,32,64} it
+ * makes one warm-up call, then `reps` timed calls (CUDA events around each
+ * one, after a write of twice the L2 size so that each call starts from HBM)
+ * on the caller's buffers, and takes the median.  The chosen s is the
+ * smallest one within 2% of the fastest median (near-ties go to the smaller
+ * block); it is recorded for this size class (log2 buckets of n and m, and p
+ * below or above 2^29) so that later s = 0 calls use it.  The per-s medians
+ * go to times_ms[7] (may be NULL; -1 where s exceeds both lengths) and the
+ * choice to *best_s.  Allocates (and frees) the flush buffer; synchronises
+ * `stream`.  reps >= 20 gives stable medians.
+ * Returns what polymul_plain returns, PM_ERR_NOMEM or PM_ERR_CUDA.
  */
 pm_status polymul_tune_plain(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64_t deg_b,
                              uint32_t *c, uint32_t p, int reps, void *stream, int *best_s,
@@ -261,6 +275,23 @@ pm_status polymul_tune_plain(const uint32_t *a, int64_t deg_a, const uint32_t *b
 
 /* Returns the s that an s = 0 call of polymul_plain would use for these sizes. */
 int polymul_plain_default_s(int64_t deg_a, int64_t deg_b, uint32_t p);
+
+/*
+ * polymul_probe_mac_rate - measures the ceiling of the plain path: how many
+ * 32 x 32 -> 64-bit multiply-adds (one per modular MAC of the s-blocked
+ * product, Section 5's multiplication phase) an SM issues per clock.  Runs
+ * blocks_per_sm x (SM count) blocks of `threads` threads, each thread adding
+ * 16 independent products per iteration for `iters` iterations, and reads
+ * every SM's cycle counter around its blocks' loops: the result, written to
+ * *macs_per_clk_sm, is the mean over the SMs of products per clock, so it
+ * does not depend on the clock.  Allocates (and frees) a small buffer;
+ * synchronises `stream`.
+ * Returns PM_OK, PM_ERR_INVALID_ARG (threads not a multiple of 32 in
+ * [32, 1024], blocks_per_sm outside [1, 32], iters < 1), PM_ERR_UNSUPPORTED
+ * (the stream captures), PM_ERR_NOMEM, PM_ERR_CUDA or PM_ERR_INTERNAL.
+ */
+pm_status polymul_probe_mac_rate(int threads, int blocks_per_sm, int64_t iters, double *macs_per_clk_sm,
+                                 void *stream);
 
 /*
  * polymul_sync_status - synchronises `stream`, then returns and clears the
@@ -280,6 +311,32 @@ int polymul_last_cuda_error(void);
 
 /* Kernel launches made by this process so far (every entry point counts its own). */
 uint64_t polymul_launch_count(void);
+
+/*
+ * polymul_debug_set - test hooks for the failure paths (the paper has no
+ * counterpart).  Process-wide; not for production use.
+ *
+ *   PM_DEBUG_FAIL_ALLOC     the next `value` device allocations the library
+ *                           makes (workspace, scratch, transform tables) fail
+ *                           as if cudaMalloc had run out of memory: the call
+ *                           that needed one returns PM_ERR_NOMEM and changes
+ *                           nothing; 0 turns the hook off.
+ *   PM_DEBUG_TC_WAIT_LIMIT  polls before a wait of the tensor-core kernel
+ *                           (polymul_batched, PM_TENSOR) is declared lost;
+ *                           0 = the built-in limit (2^26 polls).  A wait that
+ *                           runs out sets PM_ERR_TIMEOUT in the status word
+ *                           and the kernel ends its work early (outputs of the
+ *                           tiles it did not finish are left as they were);
+ *                           with value = 1 or more, the first wait of every
+ *                           role may already run out.  Whatever ran out, the
+ *                           kernel waits for the tensor-core operations it
+ *                           issued (with a limit of its own) before it frees
+ *                           its tensor memory.
+ * Returns PM_OK, or PM_ERR_INVALID_ARG for an unknown knob or value < 0.
+ */
+#define PM_DEBUG_FAIL_ALLOC 1
+#define PM_DEBUG_TC_WAIT_LIMIT 2
+pm_status polymul_debug_set(int knob, int64_t value);
 
 #ifdef __cplusplus
 }

@@ -12,6 +12,9 @@ CPU-baseline leg of ``bench.py`` may import this package.  The library in
   one division step at a time from the top as in Algorithm 1.
 * ``gcd``: the monic greatest common divisor over Z/pZ (Section 6), by the
   textbook remainder sequence.
+* ``polymul_omp``/``polymul_batch_omp``: the same definition shared out over
+  all host threads with OpenMP (``polymul_oracle_omp.c``), for timing the CPU
+  baseline only; pinned to the single-thread functions.
 * ``model``: the printed cost formulas of Section 5 and the Graham-Brent bound
   of Section 2.4 (Theorem 1, Corollary 1), in fp64.
 """
@@ -26,6 +29,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "polymul_oracle.c")
+_SRC_OMP = os.path.join(_HERE, "polymul_oracle_omp.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libpolymul_oracle.so")
 _lock = threading.Lock()
@@ -36,11 +40,15 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 
 
 def build(force: bool = False) -> str:
-    """Compiles the C oracle with gcc (plain -O2, no target-specific flags)."""
+    """Compiles the C oracle with gcc (plain -O2, no target-specific flags).  The multi-core
+    timing variants of polymul_oracle_omp.c use OpenMP where gcc has it, else one thread."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_OMP))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        base = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, _SRC_OMP]
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -80,6 +88,14 @@ def _load():
             lib.oracle_gcd.argtypes = [_u32p, ctypes.c_int64, _u32p, ctypes.c_int64, ctypes.c_uint32,
                                        _u32p, _i64p]
             lib.oracle_gcd.restype = ctypes.c_int
+            lib.oracle_omp_threads.argtypes = []
+            lib.oracle_omp_threads.restype = ctypes.c_int
+            lib.oracle_polymul_omp.argtypes = [_u32p, ctypes.c_int64, _u32p, ctypes.c_int64,
+                                               ctypes.c_uint32, _u32p]
+            lib.oracle_polymul_omp.restype = ctypes.c_int
+            lib.oracle_polymul_batch_omp.argtypes = [ctypes.c_int64, _u32p, _i64p, _u32p, _i64p, _u32p,
+                                                     _i64p, ctypes.c_uint32]
+            lib.oracle_polymul_batch_omp.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -154,6 +170,34 @@ def ntt_polymul_batch(a_data, a_off, b_data, b_off, c_off, p: int, g: int = 3) -
                                           _p(c_off, _i64p), p, g)
     if rc != 0:
         raise ValueError(f"oracle_ntt_polymul_batch failed ({rc})")
+    return f
+
+
+def omp_threads() -> int:
+    """Threads the multi-core timing variants use."""
+    return int(_load().oracle_omp_threads())
+
+
+def polymul_omp(a, b, p: int) -> np.ndarray:
+    """polymul() with its coefficients shared out over all host threads (timing only)."""
+    a, b = _u32(a), _u32(b)
+    f = np.zeros(len(a) + len(b) - 1, dtype=np.uint32)
+    rc = _load().oracle_polymul_omp(_p(a, _u32p), len(a), _p(b, _u32p), len(b), p, _p(f, _u32p))
+    if rc != 0:
+        raise ValueError("oracle_polymul_omp: bad sizes")
+    return f
+
+
+def polymul_batch_omp(a_data, a_off, b_data, b_off, c_off, p: int) -> np.ndarray:
+    """polymul_batch() with the pairs shared out over all host threads (timing only)."""
+    a_data, b_data = _u32(a_data), _u32(b_data)
+    a_off, b_off, c_off = _i64(a_off), _i64(b_off), _i64(c_off)
+    f = np.zeros(int(c_off[-1]), dtype=np.uint32)
+    rc = _load().oracle_polymul_batch_omp(len(a_off) - 1, _p(a_data, _u32p), _p(a_off, _i64p),
+                                          _p(b_data, _u32p), _p(b_off, _i64p), _p(f, _u32p),
+                                          _p(c_off, _i64p), p)
+    if rc != 0:
+        raise ValueError("oracle_polymul_batch_omp: bad sizes")
     return f
 
 

@@ -8,6 +8,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "common.cuh"
 
@@ -17,6 +18,26 @@ static std::atomic<uint64_t> g_launches{0};
 static std::atomic<int> g_last_cuda_error{0};
 static std::mutex g_ws_mutex;
 static DeviceWorkspace* g_ws[64] = {};
+// scratch buffers replaced by larger ones, per device: kept until polymul_release,
+// since a CUDA graph captured earlier may still hold their addresses
+static std::vector<void*> g_retired[64];
+
+// test hooks (polymul_debug_set)
+static std::atomic<int64_t> g_fail_alloc{0};
+static std::atomic<int64_t> g_tc_wait_limit{0};
+
+cudaError_t dev_alloc(void** ptr, size_t bytes) {
+    int64_t left = g_fail_alloc.load();
+    while (left > 0) {
+        if (g_fail_alloc.compare_exchange_weak(left, left - 1)) {
+            *ptr = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+int64_t tc_wait_limit() { return g_tc_wait_limit.load(); }
 
 pm_status cuda_fail(cudaError_t e) {
     g_last_cuda_error.store((int)e);
@@ -76,8 +97,8 @@ DeviceWorkspace* workspace(void* stream, pm_status* err) {
     w->num_sms = prop.multiProcessorCount;
     w->cc_major = prop.major;
     w->cc_minor = prop.minor;
-    e = cudaMalloc((void**)&w->status, 256);
-    if (e != cudaSuccess) { delete w; *err = PM_ERR_NOMEM; return nullptr; }
+    e = dev_alloc((void**)&w->status, 256);
+    if (e != cudaSuccess) { cudaGetLastError(); delete w; *err = PM_ERR_NOMEM; return nullptr; }
     e = cudaMemset(w->status, 0, 256);
     if (e != cudaSuccess) { cudaFree(w->status); delete w; *err = cuda_fail(e); return nullptr; }
     w->streams = new std::map<cudaStream_t, StreamScratch*>();
@@ -102,20 +123,23 @@ pm_status ensure_scratch(void** buf, size_t* have, size_t bytes, cudaStream_t st
     if (is_capturing(st)) return PM_ERR_UNSUPPORTED;
     size_t want = 4096;
     while (want < bytes) want *= 2;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= 64) return PM_ERR_INTERNAL;
     void* nb = nullptr;
-    if (cudaMalloc(&nb, want) != cudaSuccess) {
+    if (dev_alloc(&nb, want) != cudaSuccess) {
         cudaGetLastError();
         return PM_ERR_NOMEM;
     }
-    if (*buf) {
-        // work queued earlier on this stream may still use the old buffer
-        cudaStreamSynchronize(st);
-        cudaFree(*buf);
-    }
     if (zero) {
-        cudaError_t e = cudaMemsetAsync(nb, 0, want, st);
+        e = cudaMemsetAsync(nb, 0, want, st);
         if (e != cudaSuccess) { cudaFree(nb); return cuda_fail(e); }
     }
+    // The old buffer is not freed here: work queued earlier on this stream, or a
+    // CUDA graph that captured a call, may still use it.  Its counters (if any)
+    // were left at zero by every call, so such a graph stays correct.
+    if (*buf) g_retired[dev].push_back(*buf);
     *buf = nb;
     *have = want;
     return PM_OK;
@@ -301,31 +325,60 @@ pm_status polymul_tune_plain(const uint32_t* a, int64_t deg_a, const uint32_t* b
     if (rc != PM_OK) return rc;
     if (is_capturing(stream)) return PM_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
+    // Each timed launch follows a write of twice the L2 size (outside the events), so that
+    // every s is timed from HBM as a caller's first touch of its inputs would be.
+    int dev = 0, l2 = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const size_t flush_bytes = std::max<size_t>((size_t)2 * (size_t)l2, (size_t)64 << 20);
+    void* flush = nullptr;
+    if (dev_alloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return PM_ERR_NOMEM;
+    }
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError());
-    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(cudaGetLastError()); }
-    float best = 1e30f;
-    int bs = 0;
-    for (int i = 0; i < 7; ++i) {
+    if (cudaEventCreate(&e0) != cudaSuccess) { cudaFree(flush); return cuda_fail(cudaGetLastError()); }
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaFree(flush);
+        return cuda_fail(cudaGetLastError());
+    }
+    float med[7];
+    std::vector<float> ts((size_t)reps);
+    for (int i = 0; i < 7 && rc == PM_OK; ++i) {
         const int s = cand[i];
-        if (s > deg_a + 1 && s > deg_b + 1) { if (times_ms) times_ms[i] = -1.0f; continue; }
-        rc = polymul_plain(a, deg_a, b, deg_b, c, p, s, stream);
+        med[i] = -1.0f;
+        if (s > deg_a + 1 && s > deg_b + 1) continue;
+        rc = polymul_plain(a, deg_a, b, deg_b, c, p, s, stream);  // warm-up (module load, scratch)
+        for (int r = 0; r < reps && rc == PM_OK; ++r) {
+            cudaMemsetAsync(flush, r & 0xff, flush_bytes, st);
+            cudaEventRecord(e0, st);
+            rc = polymul_plain(a, deg_a, b, deg_b, c, p, s, stream);
+            cudaEventRecord(e1, st);
+            e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { rc = cuda_fail(e); break; }
+            cudaEventElapsedTime(&ts[(size_t)r], e0, e1);
+        }
         if (rc != PM_OK) break;
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < reps && rc == PM_OK; ++r) rc = polymul_plain(a, deg_a, b, deg_b, c, p, s, stream);
-        cudaEventRecord(e1, st);
-        cudaError_t e = cudaEventSynchronize(e1);
-        if (e != cudaSuccess) { rc = cuda_fail(e); break; }
-        if (rc != PM_OK) break;
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= (float)reps;
-        if (times_ms) times_ms[i] = ms;
-        if (ms < best) { best = ms; bs = s; }
+        std::sort(ts.begin(), ts.end());
+        med[i] = reps % 2 ? ts[(size_t)reps / 2] : 0.5f * (ts[(size_t)reps / 2 - 1] + ts[(size_t)reps / 2]);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaFree(flush);
     if (rc != PM_OK) return rc;
+    // the smallest s within 2% of the fastest median: near-ties go to the smaller block
+    // (fewer registers, a shorter tail), so that run-to-run noise does not flip the choice
+    float best = 1e30f;
+    for (int i = 0; i < 7; ++i)
+        if (med[i] >= 0.0f && med[i] < best) best = med[i];
+    int bs = 0;
+    for (int i = 0; i < 7 && !bs; ++i)
+        if (med[i] >= 0.0f && med[i] <= 1.02f * best) bs = cand[i];
+    if (times_ms)
+        for (int i = 0; i < 7; ++i) times_ms[i] = med[i];
     *best_s = bs;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     g_tuned[tune_key(deg_a + 1, deg_b + 1, p)] = bs;
@@ -376,6 +429,8 @@ pm_status polymul_release(void) {
             delete sc;
         }
         delete mp;
+        for (void* r : g_retired[d]) cudaFree(r);
+        g_retired[d].clear();
         delete w;
         g_ws[d] = nullptr;
     }
@@ -398,6 +453,15 @@ const char* polymul_status_string(pm_status status) {
 }
 
 int polymul_last_cuda_error(void) { return g_last_cuda_error.load(); }
+
+pm_status polymul_debug_set(int knob, int64_t value) {
+    if (value < 0) return PM_ERR_INVALID_ARG;
+    switch (knob) {
+        case PM_DEBUG_FAIL_ALLOC: g_fail_alloc.store(value); return PM_OK;
+        case PM_DEBUG_TC_WAIT_LIMIT: g_tc_wait_limit.store(value); return PM_OK;
+    }
+    return PM_ERR_INVALID_ARG;
+}
 
 uint64_t polymul_launch_count(void) { return g_launches.load(); }
 

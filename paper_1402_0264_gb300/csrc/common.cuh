@@ -112,6 +112,12 @@ pm_status stream_scratch(DeviceWorkspace* ws, cudaStream_t st, StreamScratch** o
 pm_status ensure_scratch(void** buf, size_t* have, size_t bytes, cudaStream_t st, bool zero);
 
 pm_status cuda_fail(cudaError_t e);
+// cudaMalloc, unless a test has asked for the next allocations to fail
+// (polymul_debug_set(PM_DEBUG_FAIL_ALLOC, k)).
+cudaError_t dev_alloc(void** ptr, size_t bytes);
+// Polls before a wait of the tensor-core kernel is declared lost; 0 = built-in
+// limit (polymul_debug_set(PM_DEBUG_TC_WAIT_LIMIT, k)).
+int64_t tc_wait_limit();
 void release_ntt_tables();
 void count_launches(uint64_t k);
 bool is_capturing(void* stream);

@@ -490,7 +490,7 @@ static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStrea
         ihi[f] = shoup_pair(powmod_h(wi, ((uint64_t)NTT_N2 * f) % N, p), p);
     }
     TableSet ts;
-    if (cudaMalloc((void**)&ts.dev, words * sizeof(uint2)) != cudaSuccess) {
+    if (dev_alloc((void**)&ts.dev, words * sizeof(uint2)) != cudaSuccess) {
         cudaGetLastError();
         return PM_ERR_NOMEM;
     }

@@ -1212,12 +1212,14 @@ static void* g_noalloc_ptr[64] = {};  // device address of g_noalloc_scratch, pe
 
 // Once per device, with that device current: the array's device address (the
 // host-side symbol is only a stand-in) and cleared tile counters.
-static pm_status noalloc_setup(int dev, void** out) {
+static pm_status noalloc_setup(int dev, cudaStream_t st, void** out) {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (g_noalloc_ptr[dev]) {
         *out = g_noalloc_ptr[dev];
         return PM_OK;
     }
+    // the set-up's memset and device synchronisation would break a capture
+    if (is_capturing(st)) return PM_ERR_UNSUPPORTED;
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -1275,12 +1277,12 @@ extern "C" pm_status polymul_plain_noalloc(const uint32_t* a, int64_t deg_a, con
     if (dev < 0 || dev >= 64) return PM_ERR_INTERNAL;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e);
+    cudaStream_t st = (cudaStream_t)stream;
     void* scratch = nullptr;
-    pm_status rc = noalloc_setup(dev, &scratch);
+    pm_status rc = noalloc_setup(dev, st, &scratch);
     if (rc != PM_OK) return rc;
     const uint32_t *x = a, *y = b;
     int n = (int)(deg_a + 1), m = (int)(deg_b + 1);
-    cudaStream_t st = (cudaStream_t)stream;
     switch (s) {
         case 1: return launch_pair_noalloc_s<1>(x, n, y, m, c, p, st, dev, sms, scratch);
         case 2: return launch_pair_noalloc_s<2>(x, n, y, m, c, p, st, dev, sms, scratch);

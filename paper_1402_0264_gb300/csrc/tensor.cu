@@ -70,7 +70,7 @@ constexpr int H_Q = 4 * GROUP_D + 4;                   // Hankel core-matrix ind
 constexpr int H_SLOT = H_Q * 512;                      // 4 limbs x 128-byte core matrices per index
 constexpr uint32_t TMEM_COLS = 512;                    // two accumulators of 240 columns
 constexpr uint32_t ACC_STRIDE = 256;
-constexpr int64_t WAIT_LIMIT = 1ll << 26;              // polls before a wait is declared lost
+constexpr int64_t WAIT_LIMIT = 1ll << 26;              // polls before a wait is declared lost (default)
 static_assert((BDS / 2) % 32 == 8, "limb stride must spread the limbs over the banks");
 
 // warp roles: 0 MMA issuer, 1-2 stagers (a operand), 3-6 builders (b digits,
@@ -139,9 +139,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}" ::"r"(bar) : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false if it ran out.
-__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
-    for (int64_t it = 0; it < WAIT_LIMIT; ++it) {
+// Bounded wait for phase `parity` of an mbarrier: at most `limit` polls; false
+// if it ran out.
+__device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity, int64_t limit) {
+    for (int64_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -157,11 +158,11 @@ __device__ __forceinline__ bool wait_parity(uint32_t bar, uint32_t parity) {
 // Bounded wait by lane 0; once the phase has completed every lane waits on it
 // too (returning at once), so that each reader acquires what was released
 // before the arrival.  The result is the same on all lanes.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int lane) {
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int lane, int64_t limit) {
     int ok = 1;
-    if (lane == 0) ok = wait_parity(bar, parity);
+    if (lane == 0) ok = wait_parity(bar, parity, limit);
     ok = __shfl_sync(0xffffffffu, ok, 0);
-    if (ok) wait_parity(bar, parity);
+    if (ok) wait_parity(bar, parity, WAIT_LIMIT);  // completed: returns at the first poll
     return ok != 0;
 }
 
@@ -247,6 +248,7 @@ struct TcParams {
     uint64_t off;            // a multiple of p above 2^52 (makes signed limb sums non-negative)
     uint32_t wlo[NB_LIMB];   // 256^j mod p
     uint32_t whi[NB_LIMB];   // 2^32 * 256^j mod p
+    int64_t wait_limit;      // polls before a wait between the roles is declared lost
 };
 
 // Balanced digits by an offset: with K = 32 (1 + 64 + ... + 64^4), u = v + K
@@ -354,6 +356,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(sm + SM_CTL + CTL_MISC);
     volatile int* s_abort = reinterpret_cast<volatile int*>(sm + SM_CTL + CTL_MISC + 4);
     volatile int* s_pstop = reinterpret_cast<volatile int*>(sm + SM_CTL + CTL_MISC + 8);
+    volatile int* s_sstop = reinterpret_cast<volatile int*>(sm + SM_CTL + CTL_MISC + 12);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t bar0 = smem_u32(sm + SM_CTL);
     auto bar = [bar0](int i) { return bar0 + 8u * (uint32_t)i; };
@@ -387,14 +390,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
     const int64_t total = prefix[batch];
+    const int64_t WL = tp.wait_limit;
 
     if (warp == 0) {
         // ---------------- MMA issuer ----------------
         uint32_t G = 0;  // Hankel groups consumed
         for (int k = 0;; ++k) {
             const int sb = k & 1;
-            int ok = warp_wait(bar(BAR_A_FULL + sb), (k >> 1) & 1, lane);
-            if (ok && k >= 2) ok = warp_wait(bar(BAR_ACC_EMPTY + sb), ((k >> 1) - 1) & 1, lane);
+            int ok = warp_wait(bar(BAR_A_FULL + sb), (k >> 1) & 1, lane, WL);
+            if (ok && k >= 2) ok = warp_wait(bar(BAR_ACC_EMPTY + sb), ((k >> 1) - 1) & 1, lane, WL);
             if (!ok) {
                 if (lane == 0) fail();
                 break;
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             for (int gi = 0; gi < ngroups && ok; ++gi, ++G) {
                 const int slot = (int)(G % NH);
                 if (lane == 0) {
-                    ok = wait_parity(bar(BAR_H_FULL + slot), (G / NH) & 1);
+                    ok = wait_parity(bar(BAR_H_FULL + slot), (G / NH) & 1, WL);
                     if (!ok) {
                         fail();
                     } else {
@@ -444,30 +448,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             __syncwarp();
         }
         if (lane == 0) {  // every MMA of this CTA completes before TMEM is released
+            // (with the built-in limit whatever the roles' limit is: the MMAs issued so
+            // far always complete, and TMEM must not be freed under them)
             mma_commit(bar(BAR_DRAIN));
-            if (!wait_parity(bar(BAR_DRAIN), 0)) fail();
+            if (!wait_parity(bar(BAR_DRAIN), 0, WAIT_LIMIT)) fail();
         }
         __syncwarp();
     } else if (warp < BLD_WARP0) {
         // ---------------- stagers: claim tiles, a operand ----------------
+        // The record s_tiles[sb] is rewritten only once the MMAs of the tile that
+        // used it are complete (STAGE_EMPTY), when every reader has its copy.  A
+        // stager that stops (a wait ran out, or another role failed) writes no
+        // record and arrives at nothing: the other roles then end through their
+        // own bounded waits, and no reader can see a record being rewritten.
         const int stid = tid - 32 * STG_WARP0;
         for (int k = 0;; ++k) {
             const int sb = k & 1;
             if (stid == 0) {
                 bool stop = *s_abort != 0;
-                if (!stop && k >= 2 && !wait_parity(bar(BAR_STAGE_EMPTY + sb), ((k >> 1) - 1) & 1)) {
+                if (!stop && k >= 2 && !wait_parity(bar(BAR_STAGE_EMPTY + sb), ((k >> 1) - 1) & 1, WL)) {
                     fail();
                     stop = true;
                 }
-                const int64_t tile = stop ? total : (int64_t)atomicAdd(counter, 1u);
-                TcTile tt{};
-                if (tile < total)
-                    tt = make_tile(tile, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
-                else
-                    tt.done = 1;
-                s_tiles[sb] = tt;
+                if (!stop) {
+                    const int64_t tile = (int64_t)atomicAdd(counter, 1u);
+                    TcTile tt{};
+                    if (tile < total)
+                        tt = make_tile(tile, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
+                    else
+                        tt.done = 1;
+                    s_tiles[sb] = tt;
+                }
+                *s_sstop = stop;
             }
             stagers_sync();
+            if (*s_sstop) break;  // (read by every stager before stid 0 can write it again)
             const TcTile tt = s_tiles[sb];
             if (!tt.done) {
                 stage_a(tt, sm + SM_B + sb * B_BUF, stid, tp.p);
@@ -485,7 +500,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             const int sb = k & 1;
             if (btid == 0) {
                 bool stop = *s_abort != 0;
-                if (!stop && !wait_parity(bar(BAR_A_FULL + sb), (k >> 1) & 1)) {
+                if (!stop && !wait_parity(bar(BAR_A_FULL + sb), (k >> 1) & 1, WL)) {
                     fail();
                     stop = true;
                 }
@@ -493,7 +508,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             }
             builders_sync();
             if (*s_pstop) break;
-            wait_parity(bar(BAR_A_FULL + sb), (k >> 1) & 1);  // completed: acquires the tile record
+            wait_parity(bar(BAR_A_FULL + sb), (k >> 1) & 1, WAIT_LIMIT);  // completed: acquires the tile record
             const TcTile tt = s_tiles[sb];
             if (tt.done) break;
             stage_b(tt, sbd, btid, tp.p);
@@ -504,7 +519,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                 builders_sync();  // (the b digits are complete before the first slot)
                 if (btid == 0) {
                     bool st = *s_abort != 0;
-                    if (!st && G >= NH && !wait_parity(bar(BAR_H_EMPTY + slot), ((G / NH) - 1) & 1)) {
+                    if (!st && G >= NH && !wait_parity(bar(BAR_H_EMPTY + slot), ((G / NH) - 1) & 1, WL)) {
                         fail();
                         st = true;
                     }
@@ -536,7 +551,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
         const uint32_t whi = j == 0 ? tp.whi[0] : j == 1 ? tp.whi[1] : j == 2 ? tp.whi[2] : tp.whi[3];
         for (int k = 0;; ++k) {
             const int ab = k & 1;
-            if (!warp_wait(bar(BAR_ACC_FULL + ab), (k >> 1) & 1, lane)) {
+            if (!warp_wait(bar(BAR_ACC_FULL + ab), (k >> 1) & 1, lane, WL)) {
                 if (lane == 0) fail();
                 break;
             }
@@ -678,6 +693,8 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
     tp.p = p;
     tp.mu = (uint64_t)(((unsigned __int128)1 << 64) / p);
     tp.off = ((1ull << 52) / p + 1) * (uint64_t)p;
+    const int64_t wl = tc_wait_limit();
+    tp.wait_limit = wl > 0 ? wl : WAIT_LIMIT;
     uint64_t w = 1;
     for (int j = 0; j < NB_LIMB; ++j) {
         tp.wlo[j] = (uint32_t)w;

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libpolymul.so")
 
 P_DEFAULT = 469762049
 PM_AUTO, PM_PLAIN, PM_TENSOR = 0, 1, 2
+PM_DEBUG_FAIL_ALLOC, PM_DEBUG_TC_WAIT_LIMIT = 1, 2
 S_CANDIDATES = (1, 2, 4, 8, 16, 32, 64)
 
 STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_RANGE", 3: "PM_ERR_UNSUPPORTED",
@@ -55,6 +56,8 @@ def _declare(lib):
         "polymul_status_string": ([INT], ctypes.c_char_p),
         "polymul_last_cuda_error": ([], INT),
         "polymul_launch_count": ([], ctypes.c_uint64),
+        "polymul_debug_set": ([INT, I64], INT),
+        "polymul_probe_mac_rate": ([INT, INT, I64, ctypes.POINTER(D), V], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +236,19 @@ def sync_status(stream=None) -> int:
 
 def launch_count() -> int:
     return int(lib().polymul_launch_count())
+
+
+def probe_mac_rate(threads: int = 256, blocks_per_sm: int = 4, iters: int = 20000, stream=None) -> float:
+    """32x32->64 multiply-adds per clock per SM, measured (polymul_probe_mac_rate)."""
+    r = ctypes.c_double(0.0)
+    _check(lib().polymul_probe_mac_rate(threads, blocks_per_sm, iters, ctypes.byref(r), _stream_ptr(stream)),
+           "polymul_probe_mac_rate")
+    return r.value
+
+
+def debug_set(knob: int, value: int):
+    """Test hooks of the failure paths (polymul_debug_set)."""
+    _check(lib().polymul_debug_set(knob, value), "polymul_debug_set")
 
 
 def release():

@@ -201,3 +201,16 @@ def test_planted_mistake_is_caught():
     want = (_trapezoid(n, m) % P).astype(np.uint32)
     got = _definition_with_dropped_term(np.ones(n, np.uint32), np.ones(m, np.uint32), P)
     assert not np.array_equal(got, want)
+
+
+def test_multicore_timing_variants_equal_the_definition():
+    """The OpenMP variants timed as the CPU baseline are the pinned definition shared out over
+    threads: word-for-word equal to the single-thread oracle on ragged pairs and batches."""
+    from paper_1402_0264_gb300 import inputs as _inp
+    for da, db in ((0, 0), (1, 700), (2999, 1999), (4095, 4095)):
+        a, b = _inp.poly_pair(da, db, 7000 + da)
+        assert np.array_equal(oracle.polymul_omp(a, b, P), oracle.polymul(a, b, P))
+    pk = _inp.workload_batched(batch=40)
+    assert np.array_equal(oracle.polymul_batch_omp(*pk[:4], pk[4], P),
+                          oracle.polymul_batch(*pk[:4], pk[4], P))
+    assert oracle.omp_threads() >= 1
