@@ -65,6 +65,8 @@ typedef enum {
 /* Largest supported modulus (exclusive) and degree (inclusive). */
 #define PM_MAX_P (1u << 30)
 #define PM_MAX_DEG ((int64_t)(1 << 30) - 2)
+/* Largest degree the tensor-core form takes (polymul_batched, PM_TENSOR). */
+#define PM_TENSOR_MAX_DEG ((int64_t)(1 << 24) - 1)
 
 /*
  * polymul_plain - one product by the s-blocked long multiplication
@@ -164,18 +166,22 @@ pm_status polymul_ntt(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64
  *   mode           PM_PLAIN, PM_TENSOR or PM_AUTO
  *   s              as for polymul_plain (PM_PLAIN / PM_AUTO); ignored by PM_TENSOR
  *   max_deg        an upper bound on every degree in the batch (the host cannot
- *                  read the device offsets); PM_TENSOR needs max_deg <= 4095
+ *                  read the device offsets); PM_TENSOR needs max_deg <= PM_TENSOR_MAX_DEG
  * PM_PLAIN is the s-blocked product of Section 5 with the positions of the
  * whole batch shared out: when max_deg <= 4095 and s <= 32 each warp works on
  * its own units (a small pair, or a piece of a large one), claimed from a
  * counter; otherwise each persistent CTA takes an equal range of positions.
  * The warp-level form holds up to 64 MiB of scratch per (device, stream).
  * PM_TENSOR computes the same residues on the tensor cores (bf16 limbs, fp32
- * accumulation that stays exact below 2^24); it needs p < 2^29 and
- * max_deg <= 4095, else returns PM_ERR_UNSUPPORTED.  PM_AUTO uses it when it
- * applies and max_deg > 2048 (below that the plain form measured faster).
- * With s = 0 the plain form takes the tuned s of that size class (see
- * polymul_tune_plain), else 8 from max_deg 1023 up, 4 from 63, else 2.
+ * accumulation that stays exact below 2^24: pairs whose shorter operand has
+ * more than 4096 terms are accumulated in groups of at most 4096 terms and
+ * the groups' residues added); it needs p < 2^29 and
+ * max_deg <= PM_TENSOR_MAX_DEG, else returns PM_ERR_UNSUPPORTED.  PM_AUTO uses
+ * it when it applies and max_deg > 2048 (below that the plain form measured
+ * faster).
+ * With s = 0 the plain form takes the tuned (s, Q) of the batch's size class
+ * (polymul_tune_batched), else the tuned s of a single pair of degree max_deg
+ * (polymul_tune_plain), else 8 from max_deg 1023 up, 4 from 63, else 2.
  * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_UNSUPPORTED, PM_ERR_NOMEM or PM_ERR_CUDA.
  */
 pm_status polymul_batched(int64_t batch, const uint32_t *a_data, const int64_t *a_off,
@@ -262,8 +268,9 @@ pm_status polymul_model_predict(int64_t n, int64_t m, int s, int ell, double U, 
  * one, after a write of twice the L2 size so that each call starts from HBM)
  * on the caller's buffers, and takes the median.  The chosen s is the
  * smallest one within 2% of the fastest median (near-ties go to the smaller
- * block); it is recorded for this size class (log2 buckets of n and m, and p
- * below or above 2^29) so that later s = 0 calls use it.  The per-s medians
+ * block); it is recorded in the tuners' cache (below) for this size class
+ * (device model, log2 buckets of n and m, and p below or above 2^29) so that
+ * later s = 0 calls use it.  The per-s medians
  * go to times_ms[7] (may be NULL; -1 where s exceeds both lengths) and the
  * choice to *best_s.  Allocates (and frees) the flush buffer; synchronises
  * `stream`.  reps >= 20 gives stable medians.
@@ -277,6 +284,63 @@ pm_status polymul_tune_plain(const uint32_t *a, int64_t deg_a, const uint32_t *b
 int polymul_plain_default_s(int64_t deg_a, int64_t deg_b, uint32_t p);
 
 /*
+ * polymul_tune_batched - the autotuner of the batched plain form (Section 5's
+ * block parameter s, applied per size class of a batch).  Arguments as for
+ * polymul_batched (the caller's buffers; c_data is overwritten).  For batches
+ * with max_deg <= 4095 it times the warp-level schedule for s in {2, 4, 8, 16}
+ * and unit sizes Q in {128, 256, 512, 1024, 2048} positions (the smallest
+ * piece a pair is cut into; Q also sets the claim tiers); above that, the CTA
+ * form for every s.  Each candidate: one warm-up call, then `reps` calls each
+ * after a write of twice the L2 size, the median kept.  The choice is the
+ * smallest s (then the smallest Q) within 2% of the fastest median; it is
+ * recorded for this size class (device model, p below or above 2^29, log2 of
+ * max_deg + 1 and of the batch size) and used by later calls of
+ * polymul_batched with mode PM_PLAIN or PM_AUTO's plain path and s = 0 (an
+ * explicit s keeps the tuned Q only if it equals the tuned s).  times_ms (may
+ * be NULL) receives 35 medians, index 5 i + j for s = 2^i and Q = 128 * 2^j
+ * (the CTA form: j = 1), -1 where not timed.  Allocates (and frees) the flush
+ * buffer; synchronises `stream`.
+ * Returns PM_OK, PM_ERR_INVALID_ARG (arguments, reps < 1, or the device
+ * status word set after the runs: a bad layout), PM_ERR_UNSUPPORTED (the
+ * stream captures), PM_ERR_NOMEM, PM_ERR_CUDA or PM_ERR_INTERNAL.
+ */
+pm_status polymul_tune_batched(int64_t batch, const uint32_t *a_data, const int64_t *a_off,
+                               const uint32_t *b_data, const int64_t *b_off, uint32_t *c_data,
+                               const int64_t *c_off, uint32_t p, int64_t max_deg, int reps, void *stream,
+                               int *best_s, int64_t *best_q, float *times_ms);
+
+/*
+ * The tuners' cache.  Every choice polymul_tune_plain and polymul_tune_batched
+ * make is kept in a process-wide table keyed by the device's name and SM
+ * count, the form (PM_TUNE_PLAIN: one product, buckets floor(log2 n) and
+ * floor(log2 m) of the longer and shorter operand; PM_TUNE_BATCHED: buckets
+ * floor(log2(max_deg + 1)) and floor(log2 batch)) and whether p >= 2^29.
+ * If the environment variable POLYMUL_TUNE_CACHE names a file when the table
+ * is first used, that file is loaded (a missing or unreadable file is
+ * ignored).  Host-only; no GPU needed.
+ *
+ *   polymul_tune_save    writes the table as JSON ({"version": 1, "entries":
+ *                        [...]}, one object per choice) to `path` (through a
+ *                        temporary file and a rename)
+ *   polymul_tune_load    adds the entries of a file written by
+ *                        polymul_tune_save (replacing equal keys); entries of
+ *                        other devices are kept and used only on such devices
+ *   polymul_tune_clear   empties the table (and skips the environment's file)
+ *   polymul_tune_lookup  the choice stored for an explicit device name, SM
+ *                        count, form, p and sizes (x, y = n, m or max_deg + 1,
+ *                        batch): *s = 0 and *q = 0 when there is none
+ * Return PM_OK, or PM_ERR_INVALID_ARG (null or empty path, a file that cannot
+ * be written or read, a malformed file, an unknown form).
+ */
+#define PM_TUNE_PLAIN 1
+#define PM_TUNE_BATCHED 2
+pm_status polymul_tune_save(const char *path);
+pm_status polymul_tune_load(const char *path);
+pm_status polymul_tune_clear(void);
+pm_status polymul_tune_lookup(const char *device, int sms, int form, uint32_t p, int64_t x, int64_t y, int *s,
+                              int64_t *q);
+
+/*
  * polymul_probe_mac_rate - measures the ceiling of the plain path: how many
  * 32 x 32 -> 64-bit multiply-adds (one per modular MAC of the s-blocked
  * product, Section 5's multiplication phase) an SM issues per clock.  Runs
@@ -287,7 +351,8 @@ int polymul_plain_default_s(int64_t deg_a, int64_t deg_b, uint32_t p);
  * does not depend on the clock.  Allocates (and frees) a small buffer;
  * synchronises `stream`.
  * Returns PM_OK, PM_ERR_INVALID_ARG (threads not a multiple of 32 in
- * [32, 1024], blocks_per_sm outside [1, 32], iters < 1), PM_ERR_UNSUPPORTED
+ * [32, 1024], blocks_per_sm outside [1, 32], iters outside [4, 2^32]; iters is
+ * rounded down to a multiple of 4), PM_ERR_UNSUPPORTED
  * (the stream captures), PM_ERR_NOMEM, PM_ERR_CUDA or PM_ERR_INTERNAL.
  */
 pm_status polymul_probe_mac_rate(int threads, int blocks_per_sm, int64_t iters, double *macs_per_clk_sm,

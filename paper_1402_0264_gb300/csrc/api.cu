@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "tune.cuh"
 
 namespace pm {
 
@@ -145,29 +146,10 @@ pm_status ensure_scratch(void** buf, size_t* have, size_t bytes, cudaStream_t st
     return PM_OK;
 }
 
-// ---- autotuner cache: (device, log2 n, log2 m, p >= 2^29) -> s ----
-static std::mutex g_tune_mutex;
-static std::map<std::tuple<int, int, int, int>, int> g_tuned;
-
-static int ilog2(int64_t x) {
-    int r = 0;
-    while (x > 1) { x >>= 1; ++r; }
-    return r;
-}
-
-static std::tuple<int, int, int, int> tune_key(int64_t n, int64_t m, uint32_t p) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (n < m) std::swap(n, m);
-    return std::make_tuple(dev, ilog2(n), ilog2(m), p >= (1u << 29) ? 1 : 0);
-}
-
+// ---- the block parameter an s = 0 call takes: the tuned one, else a default ----
 static int default_s(int64_t n, int64_t m, uint32_t p) {
-    {
-        std::lock_guard<std::mutex> lock(g_tune_mutex);
-        auto it = g_tuned.find(tune_key(n, m, p));
-        if (it != g_tuned.end()) return it->second;
-    }
+    TuneChoice tc;
+    if (tune_get(PM_TUNE_PLAIN, p, n, m, &tc) && tc.s > 0) return tc.s;
     const int64_t mn = n < m ? n : m;
     if (mn >= 1024) return 8;
     if (mn >= 64) return 4;
@@ -191,6 +173,27 @@ static pm_status check_pair(const uint32_t* a, int64_t deg_a, const uint32_t* b,
     if (p < 2 || p >= PM_MAX_P) return PM_ERR_RANGE;
     const int64_t L = deg_a + deg_b + 1;
     if (overlaps(c, L, a, deg_a + 1) || overlaps(c, L, b, deg_b + 1)) return PM_ERR_INVALID_ARG;
+    return PM_OK;
+}
+
+// Timing helper of the tuners: one warm-up call, then `reps` calls each after a write of
+// `flush_bytes` (outside the events); the median in *ms.
+template <typename F>
+static pm_status median_of(F call, int reps, void* flush, size_t flush_bytes, cudaStream_t st, cudaEvent_t e0,
+                           cudaEvent_t e1, std::vector<float>& ts, float* ms) {
+    pm_status rc = call();
+    for (int r = 0; r < reps && rc == PM_OK; ++r) {
+        cudaMemsetAsync(flush, r & 0xff, flush_bytes, st);
+        cudaEventRecord(e0, st);
+        rc = call();
+        cudaEventRecord(e1, st);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) return cuda_fail(e);
+        cudaEventElapsedTime(&ts[(size_t)r], e0, e1);
+    }
+    if (rc != PM_OK) return rc;
+    std::sort(ts.begin(), ts.begin() + reps);
+    *ms = reps % 2 ? ts[(size_t)reps / 2] : 0.5f * (ts[(size_t)reps / 2 - 1] + ts[(size_t)reps / 2]);
     return PM_OK;
 }
 
@@ -277,7 +280,7 @@ pm_status polymul_batched(int64_t batch, const uint32_t* a_data, const int64_t* 
     if (mode != PM_AUTO && mode != PM_PLAIN && mode != PM_TENSOR) return PM_ERR_INVALID_ARG;
     if (s != 0 && !valid_s(s)) return PM_ERR_INVALID_ARG;
     if (c_data == a_data || c_data == b_data) return PM_ERR_INVALID_ARG;
-    const bool tensor_ok = p < (1u << 29) && max_deg <= 4095;
+    const bool tensor_ok = p < (1u << 29) && max_deg <= PM_TENSOR_MAX_DEG;
     if (mode == PM_TENSOR && !tensor_ok) return PM_ERR_UNSUPPORTED;
     pm_status rc = PM_OK;
     DeviceWorkspace* ws = workspace(stream, &rc);
@@ -291,8 +294,16 @@ pm_status polymul_batched(int64_t batch, const uint32_t* a_data, const int64_t* 
                                    (cudaStream_t)stream, ws);
         if (rc != PM_ERR_UNSUPPORTED || mode == PM_TENSOR) return rc;
     }
+    // the tuned (s, Q) of this size class (polymul_tune_batched), else the defaults; an explicit s
+    // keeps the tuned Q only if it was tuned with that s
+    int64_t q = 0;
+    TuneChoice tc;
+    if (tune_get(PM_TUNE_BATCHED, p, max_deg + 1, batch, &tc) && tc.s > 0) {
+        if (s == 0) s = tc.s;
+        if (s == tc.s) q = tc.q;
+    }
     if (s == 0) s = default_s(max_deg + 1, max_deg + 1, p);
-    return launch_batched_plain(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, s, max_deg,
+    return launch_batched_plain(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, s, max_deg, q,
                                 (cudaStream_t)stream, ws);
 }
 
@@ -380,8 +391,86 @@ pm_status polymul_tune_plain(const uint32_t* a, int64_t deg_a, const uint32_t* b
     if (times_ms)
         for (int i = 0; i < 7; ++i) times_ms[i] = med[i];
     *best_s = bs;
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[tune_key(deg_a + 1, deg_b + 1, p)] = bs;
+    float bms = 0.0f;
+    for (int i = 0; i < 7; ++i)
+        if (cand[i] == bs) bms = med[i];
+    tune_put(PM_TUNE_PLAIN, p, deg_a + 1, deg_b + 1, TuneChoice{bs, 0, bms});
+    return PM_OK;
+}
+
+pm_status polymul_tune_batched(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
+                               const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
+                               const int64_t* c_off, uint32_t p, int64_t max_deg, int reps, void* stream,
+                               int* best_s, int64_t* best_q, float* times_ms) {
+    static const int scand[7] = {1, 2, 4, 8, 16, 32, 64};
+    static const int64_t qcand[5] = {128, 256, 512, 1024, 2048};
+    if (!best_s || !best_q || reps < 1 || batch < 1) return PM_ERR_INVALID_ARG;
+    if (max_deg < 0 || max_deg > PM_MAX_DEG) return PM_ERR_INVALID_ARG;
+    if (is_capturing(stream)) return PM_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    pm_status rc = PM_OK;
+    DeviceWorkspace* ws = workspace(stream, &rc);
+    if (!ws) return rc;
+    int l2 = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ws->device);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const size_t flush_bytes = std::max<size_t>((size_t)2 * (size_t)l2, (size_t)64 << 20);
+    void* flush = nullptr;
+    if (dev_alloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return PM_ERR_NOMEM;
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) { cudaFree(flush); return cuda_fail(cudaGetLastError()); }
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaFree(flush);
+        return cuda_fail(cudaGetLastError());
+    }
+    // the warp-level schedule (degrees below 4096, s <= 16 here) has the unit size to tune; the
+    // CTA form only s
+    const bool warp_form = max_deg <= 4095;
+    float med[7][5];
+    std::vector<float> ts((size_t)reps);
+    for (int i = 0; i < 7 && rc == PM_OK; ++i) {
+        for (int j = 0; j < 5 && rc == PM_OK; ++j) {
+            med[i][j] = -1.0f;
+            const int sv = scand[i];
+            if (warp_form ? (sv < 2 || sv > 16) : j != 1) continue;
+            if (sv > max_deg + 1) continue;
+            const int64_t qv = warp_form ? qcand[j] : 0;
+            auto call = [&]() {
+                return launch_batched_plain(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, sv, max_deg, qv,
+                                            st, ws);
+            };
+            rc = median_of(call, reps, flush, flush_bytes, st, e0, e1, ts, &med[i][j]);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(flush);
+    if (rc != PM_OK) return rc;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int v = 0;  // a bad layout, found on the device, leaves nothing to choose from
+    e = cudaMemcpy(&v, ws->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (v != 0) return PM_ERR_INVALID_ARG;
+    float best = 1e30f;
+    for (int i = 0; i < 7; ++i)
+        for (int j = 0; j < 5; ++j)
+            if (med[i][j] >= 0.0f && med[i][j] < best) best = med[i][j];
+    int bi = -1, bj = -1;  // the first (smallest s, then smallest Q) within 2% of the fastest
+    for (int i = 0; i < 7 && bi < 0; ++i)
+        for (int j = 0; j < 5 && bi < 0; ++j)
+            if (med[i][j] >= 0.0f && med[i][j] <= 1.02f * best) { bi = i; bj = j; }
+    if (bi < 0) return PM_ERR_INTERNAL;
+    if (times_ms)
+        for (int i = 0; i < 7; ++i)
+            for (int j = 0; j < 5; ++j) times_ms[5 * i + j] = med[i][j];
+    *best_s = scand[bi];
+    *best_q = warp_form ? qcand[bj] : 0;
+    tune_put(PM_TUNE_BATCHED, p, max_deg + 1, batch, TuneChoice{*best_s, *best_q, med[bi][bj]});
     return PM_OK;
 }
 

@@ -125,9 +125,10 @@ bool is_capturing(void* stream);
 // Kernel launchers (one translation unit each).
 pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c,
                        uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws);
+// q_min: the smallest unit (positions) of the warp-level schedule; 0 = the default
 pm_status launch_batched_plain(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
-                               const int64_t* c_off, uint32_t p, int s, int64_t max_deg,
+                               const int64_t* c_off, uint32_t p, int s, int64_t max_deg, int64_t q_min,
                                cudaStream_t st, DeviceWorkspace* ws);
 pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c,
                      uint32_t p, uint32_t g, cudaStream_t st, DeviceWorkspace* ws);

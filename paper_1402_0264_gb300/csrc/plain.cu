@@ -882,7 +882,8 @@ __device__ __forceinline__ void block_scan3(long long& x0, long long& x1, long l
 }
 
 #ifndef PM_PLAIN_STUDY_TU
-__global__ void __launch_bounds__(PLAN_THREADS) warp_plan_kernel(int batch, int td, WkPlan pl, int* status) {
+__global__ void __launch_bounds__(PLAN_THREADS) warp_plan_kernel(int batch, int td, int64_t q_min, WkPlan pl,
+                                                                  int* status) {
     // pairs in rounds of PLAN_THREADS, pair r PLAN_THREADS + tid by thread tid
     __shared__ long long s_scan[96];
     __shared__ int s_bad;
@@ -901,7 +902,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) warp_plan_kernel(int batch, int 
     const int64_t G = s_g;
     const int64_t umax = wk_units_max(td);
     // pieces cut only pairs of more than Q positions: at most 2 G / Q of them
-    const int64_t Q = max(WK_MIN_UNIT, (2 * G + umax - 1) / umax);
+    const int64_t Q = max(q_min, (2 * G + umax - 1) / umax);
     if (tid == 0) s_bad = 0;
     __syncthreads();
     // running totals of positions, pieces, tier-1 and tier-2 pairs
@@ -968,6 +969,87 @@ __global__ void __launch_bounds__(256) warp_fill_kernel(int batch, WkPlan pl) {
     }
     const int64_t k0 = pl.kbase[i], k1 = pl.kbase[i + 1];
     for (int64_t k = k0 + lane; k < k1; k += 32) pl.unit_pair[k] = i;
+}
+#endif  // PM_PLAIN_STUDY_TU
+
+// The three planning steps in one CTA, for batches of at most WK_FUSED_MAX
+// pairs (one launch instead of three): the position count of every pair and
+// their total, then the scans of warp_plan_kernel (each thread keeps the pairs
+// it counted), then the unit table of warp_fill_kernel and the claim counter.
+constexpr int WK_FUSED_MAX = 32768;
+#ifndef PM_PLAIN_STUDY_TU
+__global__ void __launch_bounds__(PLAN_THREADS) warp_plan_fused_kernel(
+    int batch, const int64_t* __restrict__ a_off, const int64_t* __restrict__ b_off,
+    const int64_t* __restrict__ c_off, int64_t max_deg, int td, int64_t q_min, WkPlan pl, int* status) {
+    __shared__ long long s_scan[96];
+    __shared__ int s_bad;
+    __shared__ long long s_round[4];
+    __shared__ long long s_g;
+    const int tid = threadIdx.x;
+    const int rounds = (batch + PLAN_THREADS - 1) / PLAN_THREADS;
+    if (tid == 0) s_bad = 0;
+    {
+        long long t = 0;  // pair r PLAN_THREADS + tid is counted by thread tid (and read back by it below)
+        for (int i = tid; i < batch; i += PLAN_THREADS) {
+            int64_t n, m;
+            const int64_t np = pair_dims(i, a_off, b_off, c_off, max_deg, &n, &m) ? pair_positions(n, m, td) : -1;
+            pl.pos[i] = np;
+            if (np > 0) t += np;
+        }
+        long long d1 = 0, d2 = 0;
+        block_scan3(t, d1, d2, s_scan);
+        if (tid == PLAN_THREADS - 1) s_g = t;
+        __syncthreads();
+    }
+    const int64_t G = s_g;
+    const int64_t umax = wk_units_max(td);
+    const int64_t Q = max(q_min, (2 * G + umax - 1) / umax);
+    long long bp = 0, b0 = 0, b1 = 0, b2 = 0;
+    for (int r = 0; r < rounds; ++r) {
+        const int i = r * PLAN_THREADS + tid;
+        const int64_t np = i < batch ? pl.pos[i] : 0;
+        if (np < 0) s_bad = 1;
+        const int tier = (i >= batch || np < 0) ? 3 : (np > Q ? 0 : (8 * np >= Q ? 1 : 2));
+        const long long nu = tier == 0 ? div_up(np, Q) : 0;
+        long long xp = np > 0 ? np : 0, x0 = nu, x1 = tier == 1;
+        block_scan3(xp, x0, x1, s_scan);
+        long long x2 = tier == 2, d1 = 0, d2 = 0;
+        block_scan3(x2, d1, d2, s_scan);
+        if (i < batch) {
+            pl.pos[i] = bp + xp - (np > 0 ? np : 0);
+            pl.kbase[i] = b0 + x0 - nu;
+            pl.rank[i] = tier == 1 ? b1 + x1 - 1 : (tier == 2 ? b2 + x2 - 1 : -1);
+        }
+        if (tid == PLAN_THREADS - 1) { s_round[0] = xp; s_round[1] = x0; s_round[2] = x1; s_round[3] = x2; }
+        __syncthreads();
+        bp += s_round[0];
+        b0 += s_round[1];
+        b1 += s_round[2];
+        b2 += s_round[3];
+        __syncthreads();
+    }
+    const bool bad = s_bad != 0;
+    if (tid == 0) {
+        if (bad) atomicCAS(status, 0, (int)PM_ERR_INVALID_ARG);
+        pl.pos[batch] = G;
+        pl.kbase[batch] = b0;
+        pl.sched[0] = Q;
+        pl.sched[1] = bad ? 0 : b0;  // nothing is computed for an invalid batch
+        pl.sched[2] = bad ? 0 : b1;
+        pl.sched[3] = bad ? 0 : b2;
+        pl.sched[4] = 0;             // claim counter
+    }
+    __syncthreads();  // the prefix, bases and ranks of every pair are visible to the whole CTA
+    if (bad) return;
+    for (int i = tid; i < batch; i += PLAN_THREADS) {
+        const int64_t rk = pl.rank[i];
+        if (rk >= 0) {
+            const int64_t np = pl.pos[i + 1] - pl.pos[i];
+            pl.unit_pair[(8 * np >= Q ? b0 : b0 + b1) + rk] = i;
+        } else {
+            for (int64_t k = pl.kbase[i]; k < pl.kbase[i + 1]; ++k) pl.unit_pair[k] = i;
+        }
+    }
 }
 #endif  // PM_PLAIN_STUDY_TU
 
@@ -1068,7 +1150,7 @@ pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t 
 template <int S>
 static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                        const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
-                                       const int64_t* c_off, uint32_t p, int64_t max_deg,
+                                       const int64_t* c_off, uint32_t p, int64_t max_deg, int64_t q_min,
                                        cudaStream_t st, DeviceWorkspace* ws) {
     using W = WCfg<S>;
     auto kern = plain_warp_kernel<S>;
@@ -1097,10 +1179,18 @@ static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, co
     pl.rank = pl.kbase + (batch + 1);
     pl.bsum = pl.rank + batch;
     pl.unit_pair = reinterpret_cast<int*>(pl.bsum + nblk);
-    warp_count_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg,
-                                                                      W::TD, pl.pos, pl.bsum);
-    warp_plan_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, W::TD, pl, ws->status);
-    warp_fill_kernel<<<(unsigned)((batch + 7) / 8), 256, 0, st>>>((int)batch, pl);
+    const int64_t qm = q_min > 0 ? q_min : WK_MIN_UNIT;
+    int plan_launches = 1;
+    if (batch <= WK_FUSED_MAX) {
+        warp_plan_fused_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg, W::TD, qm, pl,
+                                                           ws->status);
+    } else {
+        warp_count_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>((int)batch, a_off, b_off, c_off,
+                                                                          max_deg, W::TD, pl.pos, pl.bsum);
+        warp_plan_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, W::TD, qm, pl, ws->status);
+        warp_fill_kernel<<<(unsigned)((batch + 7) / 8), 256, 0, st>>>((int)batch, pl);
+        plan_launches = 3;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     const ModParams mp = host_mod_params(p, Cfg<S>::KB);
@@ -1108,7 +1198,7 @@ static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, co
                                                           mp, sk);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
-    count_launches(4);
+    count_launches(1 + plan_launches);
     return PM_OK;
 }
 
@@ -1116,10 +1206,11 @@ static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, co
 template <int S>
 static pm_status launch_batched_s(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                   const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
-                                  const int64_t* c_off, uint32_t p, int64_t max_deg,
+                                  const int64_t* c_off, uint32_t p, int64_t max_deg, int64_t q_min,
                                   cudaStream_t st, DeviceWorkspace* ws) {
     if (max_deg <= WK_MAX_DEG && S <= 32)  // (64 sums per lane would spill in the warp form)
-        return launch_batched_warp_s<S>(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, st, ws);
+        return launch_batched_warp_s<S>(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, q_min, st,
+                                        ws);
     using C = Cfg<S>;
     auto kern = plain_sk_kernel<S, true>;
     static int occ_cache[64] = {};
@@ -1152,12 +1243,12 @@ static pm_status launch_batched_s(int64_t batch, const uint32_t* a_data, const i
 #ifndef PM_PLAIN_STUDY_TU
 pm_status launch_batched_plain(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
-                               const int64_t* c_off, uint32_t p, int s, int64_t max_deg,
+                               const int64_t* c_off, uint32_t p, int s, int64_t max_deg, int64_t q_min,
                                cudaStream_t st, DeviceWorkspace* ws) {
     switch (s) {
 #define PM_CASE(SV) \
     case SV:        \
-        return launch_batched_s<SV>(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, st, ws);
+        return launch_batched_s<SV>(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, q_min, st, ws);
         PM_CASE(1) PM_CASE(2) PM_CASE(4) PM_CASE(8) PM_CASE(16) PM_CASE(32) PM_CASE(64)
 #undef PM_CASE
         default: return PM_ERR_INVALID_ARG;

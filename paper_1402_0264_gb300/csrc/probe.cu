@@ -37,10 +37,16 @@ __global__ void mac_probe_kernel(const uint32_t* __restrict__ seed, int64_t iter
     __syncthreads();
     long long t0 = 0;
     if (threadIdx.x == 0) t0 = clock64();
-    for (int64_t it = 0; it < iters; ++it) {
+    // four iterations per trip of a 32-bit loop, so that the loop's own instructions stay
+    // a few per 64 products
+    const int trips = (int)(iters >> 2);
+    for (int it = 0; it < trips; ++it) {
 #pragma unroll
-        for (int e = 0; e < PROBE_SUMS; ++e) acc[e] = mad_wide(x[e], y, acc[e]);
-        y += 0x9e3779b9u;  // new products every iteration (one add per 16 products)
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int e = 0; e < PROBE_SUMS; ++e) acc[e] = mad_wide(x[e], y, acc[e]);
+            y += 0x9e3779b9u;  // new products every iteration (one add per 16 products)
+        }
     }
     __syncthreads();
     uint64_t t = 0;
@@ -63,7 +69,7 @@ using namespace pm;
 extern "C" pm_status polymul_probe_mac_rate(int threads, int blocks_per_sm, int64_t iters, double* macs_per_clk_sm,
                                             void* stream) {
     if (!macs_per_clk_sm || threads < 32 || threads > 1024 || threads % 32 || blocks_per_sm < 1 ||
-        blocks_per_sm > 32 || iters < 1)
+        blocks_per_sm > 32 || iters < 4 || iters > ((int64_t)1 << 32))
         return PM_ERR_INVALID_ARG;
     if (is_capturing(stream)) return PM_ERR_UNSUPPORTED;
     int dev = 0, sms = 0;
@@ -121,7 +127,7 @@ extern "C" pm_status polymul_probe_mac_rate(int threads, int blocks_per_sm, int6
     for (const auto& kv : per_sm) {
         const Span& sp = kv.second;
         if (sp.hi <= sp.lo) continue;
-        sum += (double)sp.cnt * threads * (double)iters * PROBE_SUMS / (double)(sp.hi - sp.lo);
+        sum += (double)sp.cnt * threads * (double)(iters / 4 * 4) * PROBE_SUMS / (double)(sp.hi - sp.lo);
         ++used;
     }
     if (!used) return PM_ERR_INTERNAL;

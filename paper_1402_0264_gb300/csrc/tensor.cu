@@ -9,9 +9,14 @@
 // [-128, 127], a into 5 balanced base-64 digits e_i in [-32, 31]; bf16 holds
 // both exactly.  Then
 //     c = sum_{i<5, j<4} 64^i 256^j (e_i * d_j)   (mod p),
-// and every entry of a digit convolution e_i * d_j is a sum of at most
-// min(n, m) <= 4096 products of magnitude <= 128 * 32 = 2^12, so it stays
-// within 2^24 in magnitude and the tensor core's fp32 accumulation is exact.
+// and every entry of a digit convolution e_i * d_j accumulated over a group of
+// shifts is a sum of products of magnitude <= 128 * 32 = 2^12, one for each
+// index of b the group's shifts reach (at most min(n, m), and at most 32 per
+// shift): with at most 4096 terms it stays within 2^24 in magnitude and the
+// tensor core's fp32 accumulation is exact.  A tile whose shifts reach more
+// than 4096 indices of both operands (min(n, m) > 4096) is done in K-groups of
+// at most 128 shifts, each accumulated on its own and reduced mod p, the
+// later groups added onto the earlier groups' residues in the epilogue.
 // (tcgen05 kind::i8 would hold larger limbs, but ptxas rejects it for
 // sm_103a.)
 //
@@ -41,7 +46,8 @@
 // added with two warp shuffles before the store.
 //
 // Work: tiles of 1536 outputs of every pair, taken by persistent CTAs (one
-// per SM) from an atomic counter.  Every wait on an mbarrier is bounded: when
+// per SM) from an atomic counter; the K-groups of a tile run one after the
+// other on the CTA that took it.  Every wait on an mbarrier is bounded: when
 // it runs out the kernel records PM_ERR_TIMEOUT and skips the remaining work.
 #include <cuda_bf16.h>
 
@@ -56,7 +62,9 @@ constexpr int NBLK = 48;                   // blocks per tile
 constexpr int NA_LIMB = 5, NB_LIMB = 4;
 constexpr int MMA_M = 128, MMA_N = NBLK * NA_LIMB;  // 240
 constexpr int TILE_OUT = TT * NBLK;        // 1536
-constexpr int TC_MAXK = 4096;              // exactness bound on min(n, m)
+constexpr int TC_MAXK = 4096;              // exactness bound: terms per accumulated entry
+constexpr int TC_GROUP = TC_MAXK / TT;     // shifts per K-group when both operands are longer
+constexpr int64_t TC_MAX_DEG = PM_TENSOR_MAX_DEG;      // degrees this path takes (int tile indices)
 constexpr int GROUP_D = 8;                 // shifts per Hankel slot
 constexpr int NH = 4;                      // Hankel slots in the ring
 constexpr int MAX_DELTA = TC_MAXK / TT + 2;            // shifts a tile can need
@@ -114,9 +122,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
-// instruction descriptor: D f32, A and B bf16, both K-major, N and M as given
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
-                           ((uint32_t)(MMA_M >> 4) << 24);
+// instruction descriptor: D f32, A and B bf16, both K-major, M = 128; the N field
+// (bits 17-22, N / 8) is or-ed in per MMA (N a multiple of 16, at most 240)
+constexpr uint32_t IDESC_BASE = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MMA_M >> 4) << 24);
+
+#ifndef PM_TC_NARROW
+#define PM_TC_NARROW 0  // 1: MMAs cover only the columns a shift meets (build-time choice)
+#endif
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
     asm volatile(
@@ -199,13 +211,14 @@ struct TcTile {
     const uint32_t* b;
     uint32_t* c;
     int n, m, L, I0, na, d_lo, d_hi, nd, J_min, nJ, tb0, done;
+    int acc;   // a later K-group: add onto the residues already in c
 };
 static_assert(2 * sizeof(TcTile) <= CTL_EPI - CTL_TILES, "control block");
 
 // what the epilogue needs of a tile
 struct EpiInfo {
     uint32_t* c;
-    int L, I0, done;
+    int L, I0, done, acc;
 };
 static_assert(2 * sizeof(EpiInfo) <= CTL_MISC - CTL_EPI, "control block");
 
@@ -239,7 +252,28 @@ __device__ __forceinline__ TcTile make_tile(int64_t tile, int batch, const uint3
     tt.nJ = NBLK + tt.d_hi - tt.d_lo;                   // blocks J_min .. J_min + nJ - 1
     tt.tb0 = TT * tt.d_lo - TT;                         // first staged b index
     tt.done = 0;
+    tt.acc = 0;
     return tt;
+}
+
+// K-groups of a tile: one group when b (the shorter operand) has at most TC_MAXK
+// terms, else groups of at most TC_GROUP shifts of about equal size.
+__device__ __forceinline__ int tile_groups(const TcTile& t) {
+    return t.m <= TC_MAXK ? 1 : (t.nd + TC_GROUP - 1) / TC_GROUP;
+}
+
+// Group g of ng of the tile: its shifts d_lo .. d_hi and the a blocks and b digits they use.
+__device__ __forceinline__ TcTile sub_tile(const TcTile& t, int g, int ng) {
+    TcTile u = t;
+    const int gsz = (t.nd + ng - 1) / ng;
+    u.d_lo = t.d_lo + g * gsz;
+    u.d_hi = min(t.d_hi, u.d_lo + gsz - 1);
+    u.nd = u.d_hi - u.d_lo + 1;
+    u.J_min = u.I0 - u.d_hi;
+    u.nJ = NBLK + u.d_hi - u.d_lo;
+    u.tb0 = TT * u.d_lo - TT;
+    u.acc = g > 0;
+    return u;
 }
 
 struct TcParams {
@@ -348,7 +382,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     int batch, const uint32_t* __restrict__ a_data, const int64_t* __restrict__ a_off,
     const uint32_t* __restrict__ b_data, const int64_t* __restrict__ b_off,
     uint32_t* __restrict__ c_data, const int64_t* __restrict__ c_off, const int64_t* __restrict__ prefix,
-    unsigned int* __restrict__ counter, TcParams tp, int* status) {
+    unsigned long long* __restrict__ counter, TcParams tp, int* status) {
     extern __shared__ __align__(1024) uint8_t sm[];
     uint16_t* sbd = reinterpret_cast<uint16_t*>(sm + SM_BD);
     TcTile* s_tiles = reinterpret_cast<TcTile*>(sm + SM_CTL + CTL_TILES);
@@ -405,7 +439,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             }
             const TcTile tt = s_tiles[sb];
             if (lane == 0) {
-                s_epi[sb] = EpiInfo{tt.c, tt.L, tt.I0, tt.done};
+                s_epi[sb] = EpiInfo{tt.c, tt.L, tt.I0, tt.done, tt.acc};
                 mbar_arrive(bar(BAR_ACC_FULL + sb));  // the record (the second arrival is the MMAs')
                 if (tt.done) mbar_arrive(bar(BAR_ACC_FULL + sb));
             }
@@ -425,14 +459,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                         const int nds = min(GROUP_D, tt.nd - gi * GROUP_D);
                         const int dg = tt.d_lo + gi * GROUP_D;
                         for (int s = 0; s < nds; ++s) {
-                            // every shift spans all 240 columns (narrower MMAs for the blocks a
-                            // shift meets measured slower per product on this part)
-                            const uint32_t b_addr = sBa + (uint32_t)(NA_LIMB * (tt.d_hi - dg - s) * 16);
+                            const bool first = gi == 0 && s == 0;
+                            uint32_t c0 = 0, nc = MMA_N;  // columns of this shift's MMAs
+#if PM_TC_NARROW
+                            // Shift d meets the tile's blocks lo .. hi (those whose block of a,
+                            // I - d, exists and which hold outputs); its MMAs cover their
+                            // columns, widened to multiples of 16.  The first shift spans all
+                            // 240 columns, since it initialises the accumulator.
+                            if (!first) {
+                                const int d = dg + s;
+                                const int lo = max(0, d - tt.I0);
+                                const int hi = min(min(NBLK - 1, d + tt.na - 1 - tt.I0), (tt.L - 1) / TT - tt.I0);
+                                if (hi < lo) continue;  // no output of the tile gets a term from this shift
+                                c0 = (uint32_t)(NA_LIMB * lo) & ~15u;
+                                nc = min((uint32_t)MMA_N, (uint32_t)(NA_LIMB * hi + NA_LIMB + 15) & ~15u) - c0;
+                            }
+#endif
+                            const uint32_t idesc = IDESC_BASE | ((nc >> 3) << 17);
+                            const uint32_t b_addr = sBa + (uint32_t)((NA_LIMB * (tt.d_hi - dg - s) + (int)c0) * 16);
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 const uint64_t da = smem_desc(ha + (uint32_t)((4 * s + 2 * h) * 512), 512, 128);
                                 const uint64_t db = smem_desc(b_addr + 2 * h * B_LBO, B_LBO, 128);
-                                mma_bf16(tacc, da, db, IDESC, (gi == 0 && s == 0 && h == 0) ? 0u : 1u);
+                                mma_bf16(tacc + c0, da, db, idesc, (first && h == 0) ? 0u : 1u);
                             }
                         }
                         mma_commit(bar(BAR_H_EMPTY + slot));
@@ -461,7 +510,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
         // stager that stops (a wait ran out, or another role failed) writes no
         // record and arrives at nothing: the other roles then end through their
         // own bounded waits, and no reader can see a record being rewritten.
+        // Each claimed tile is handed on as its K-groups, one record per group.
         const int stid = tid - 32 * STG_WARP0;
+        TcTile cur{};       // the claimed tile (stid 0 only)
+        int g = 0, ng = 0;  // its next group and number of groups
         for (int k = 0;; ++k) {
             const int sb = k & 1;
             if (stid == 0) {
@@ -471,12 +523,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                     stop = true;
                 }
                 if (!stop) {
-                    const int64_t tile = (int64_t)atomicAdd(counter, 1u);
                     TcTile tt{};
-                    if (tile < total)
-                        tt = make_tile(tile, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
-                    else
-                        tt.done = 1;
+                    if (g >= ng) {  // claim the next tile
+                        const int64_t tile = (int64_t)atomicAdd(counter, 1ull);
+                        if (tile < total) {
+                            cur = make_tile(tile, batch, a_data, a_off, b_data, b_off, c_data, c_off, prefix);
+                            g = 0;
+                            ng = tile_groups(cur);
+                        } else {
+                            tt.done = 1;
+                        }
+                    }
+                    if (!tt.done) tt = sub_tile(cur, g++, ng);
                     s_tiles[sb] = tt;
                 }
                 *s_sstop = stop;
@@ -605,7 +663,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                     const uint64_t z = (o2 ? y1 : y0) + __shfl_xor_sync(0xffffffffu, o2 ? y0 : y1, 16);  // < 2^64
                     const int blk = NBLK / 2 * half + 8 * rd + 4 * c4 + j;
                     const int g = (info.I0 + blk) * TT + r;
-                    if (g < info.L) info.c[g] = barrett(z, tp.p, tp.mu);
+                    if (g < info.L) {
+                        // a later K-group adds onto the residue this thread wrote for the earlier
+                        // groups (same thread, same word: program order); z < 2^63.01
+                        const uint64_t prev = info.acc ? (uint64_t)info.c[g] : 0ull;
+                        info.c[g] = barrett(z + prev, tp.p, tp.mu);
+                    }
                 }
             }
         }
@@ -623,7 +686,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
 __global__ void __launch_bounds__(1024) tc_plan_kernel(int batch, const int64_t* __restrict__ a_off,
                                                         const int64_t* __restrict__ b_off,
                                                         const int64_t* __restrict__ c_off, int64_t max_deg,
-                                                        int64_t* prefix, unsigned int* counter, int* status) {
+                                                        int64_t* prefix, unsigned long long* counter, int* status) {
     __shared__ long long s_scan[1024];
     __shared__ int s_bad;
     const int tid = threadIdx.x;
@@ -673,14 +736,14 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
                                 const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                 const int64_t* c_off, uint32_t p, int64_t max_deg, cudaStream_t st,
                                 DeviceWorkspace* ws) {
-    if (p >= (1u << 29) || max_deg + 1 > TC_MAXK) return PM_ERR_UNSUPPORTED;
+    if (p >= (1u << 29) || max_deg > TC_MAX_DEG) return PM_ERR_UNSUPPORTED;
     if (ws->cc_major != 10) return PM_ERR_UNSUPPORTED;  // tcgen05 needs the sm_100 family
     StreamScratch* sc = nullptr;
     pm_status rc = stream_scratch(ws, st, &sc);
     if (rc != PM_OK) return rc;
     rc = ensure_scratch(&sc->tc, &sc->tc_bytes, 256 + sizeof(int64_t) * (size_t)(batch + 1), st, false);
     if (rc != PM_OK) return rc;
-    unsigned int* counter = reinterpret_cast<unsigned int*>(sc->tc);
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(sc->tc);
     int64_t* prefix = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(sc->tc) + 256);
     static int done[64] = {};
     cudaError_t e;

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libpolymul.so")
 P_DEFAULT = 469762049
 PM_AUTO, PM_PLAIN, PM_TENSOR = 0, 1, 2
 PM_DEBUG_FAIL_ALLOC, PM_DEBUG_TC_WAIT_LIMIT = 1, 2
+PM_TUNE_PLAIN, PM_TUNE_BATCHED = 1, 2
+Q_CANDIDATES = (128, 256, 512, 1024, 2048)
 S_CANDIDATES = (1, 2, 4, 8, 16, 32, 64)
 
 STATUS = {0: "PM_OK", 1: "PM_ERR_INVALID_ARG", 2: "PM_ERR_RANGE", 3: "PM_ERR_UNSUPPORTED",
@@ -58,6 +60,13 @@ def _declare(lib):
         "polymul_launch_count": ([], ctypes.c_uint64),
         "polymul_debug_set": ([INT, I64], INT),
         "polymul_probe_mac_rate": ([INT, INT, I64, ctypes.POINTER(D), V], INT),
+        "polymul_tune_batched": ([I64, V, V, V, V, V, V, U32, I64, INT, V, ctypes.POINTER(INT),
+                                  ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_float)], INT),
+        "polymul_tune_save": ([ctypes.c_char_p], INT),
+        "polymul_tune_load": ([ctypes.c_char_p], INT),
+        "polymul_tune_clear": ([], INT),
+        "polymul_tune_lookup": ([ctypes.c_char_p, INT, INT, U32, I64, I64, ctypes.POINTER(INT),
+                                 ctypes.POINTER(I64)], INT),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -223,6 +232,48 @@ def tune_plain(a, b, p: int = P_DEFAULT, reps: int = 5, out=None, stream=None):
                                     _stream_ptr(stream), ctypes.byref(best), times),
            "polymul_tune_plain")
     return best.value, {s: t for s, t in zip(S_CANDIDATES, list(times)) if t >= 0}
+
+
+def tune_batched(a_data, a_off, b_data, b_off, c_off, max_deg: int, p: int = P_DEFAULT, reps: int = 20,
+                 out=None, total: int | None = None, stream=None):
+    """The batched autotuner: returns (best_s, best_q, {(s, q): median ms}) and records the choice."""
+    batch = a_off.numel() - 1
+    if total is None:
+        total = int(c_off[-1].item())
+    out = _alloc(total, a_data) if out is None else out
+    bs, bq = ctypes.c_int(0), ctypes.c_int64(0)
+    times = (ctypes.c_float * 35)()
+    _check(lib().polymul_tune_batched(batch, _dev_words(a_data, "a_data"), _dev_i64(a_off, "a_off"),
+                                      _dev_words(b_data, "b_data"), _dev_i64(b_off, "b_off"),
+                                      _dev_words(out, "out"), _dev_i64(c_off, "c_off"), p, max_deg, reps,
+                                      _stream_ptr(stream), ctypes.byref(bs), ctypes.byref(bq), times),
+           "polymul_tune_batched")
+    res = {}
+    for i, sv in enumerate(S_CANDIDATES):
+        for j, qv in enumerate(Q_CANDIDATES):
+            if times[5 * i + j] >= 0:
+                res[(sv, qv)] = times[5 * i + j]
+    return bs.value, bq.value, res
+
+
+def tune_save(path: str):
+    _check(lib().polymul_tune_save(path.encode()), "polymul_tune_save")
+
+
+def tune_load(path: str):
+    _check(lib().polymul_tune_load(path.encode()), "polymul_tune_load")
+
+
+def tune_clear():
+    _check(lib().polymul_tune_clear(), "polymul_tune_clear")
+
+
+def tune_lookup(device: str, sms: int, form: int, p: int, x: int, y: int):
+    """The cached (s, q) for an explicit device and size class; (0, 0) if none (host-only)."""
+    s_, q_ = ctypes.c_int(0), ctypes.c_int64(0)
+    _check(lib().polymul_tune_lookup(device.encode(), sms, form, p, x, y, ctypes.byref(s_), ctypes.byref(q_)),
+           "polymul_tune_lookup")
+    return s_.value, q_.value
 
 
 def default_s(deg_a: int, deg_b: int, p: int = P_DEFAULT) -> int:

@@ -37,6 +37,13 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), f"{name} declared in include/ but not exported"
 
 
+def test_debug_knob_validation(lib):
+    assert lib.polymul_debug_set(99, 1) == 1                   # unknown knob
+    assert lib.polymul_debug_set(pm.PM_DEBUG_FAIL_ALLOC, -1) == 1
+    assert lib.polymul_debug_set(pm.PM_DEBUG_TC_WAIT_LIMIT, 0) == 0
+    assert lib.polymul_debug_set(pm.PM_DEBUG_FAIL_ALLOC, 0) == 0
+
+
 def test_status_strings(lib):
     for code in range(8):
         assert lib.polymul_status_string(code)
@@ -72,7 +79,7 @@ def test_batched_validation_happens_on_host(lib):
     assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 7, 1, 0, -1, NULL) == 1  # bad max_deg
     # tensor mode outside its exactness bounds
     assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 2**29 + 11, 2, 0, 100, NULL) == 3
-    assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 7, 2, 0, 4096, NULL) == 3
+    assert f(4, FAKE, FAKE, FAKE, FAKE, FAKE2, FAKE, 7, 2, 0, 2**24, NULL) == 3
 
 
 def test_ntt_validation_happens_on_host(lib):

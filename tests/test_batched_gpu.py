@@ -110,3 +110,39 @@ def test_graph_capture_replay():
         out.zero_()
         g.replay()
         assert_equal(host(out), want, "graph replay")
+
+
+def test_batched_tuner_records_and_uses_its_choice(tmp_path):
+    """polymul_tune_batched times (s, Q) on the warp-level schedule, records the choice for the batch's size
+    class, and s = 0 calls then run with it and stay exact; the choice survives a save and a load."""
+    import torch
+    packed = inputs.workload_batched(batch=500)
+    want = oracle.polymul_batch(*packed[:4], packed[4], P)
+    t = [dev(packed[0]), dev64(packed[1]), dev(packed[2]), dev64(packed[3]), dev64(packed[4])]
+    pm.tune_clear()
+    best_s, best_q, times = pm.tune_batched(*t, max_deg=2048, reps=3, total=int(packed[4][-1]))
+    assert best_s in (2, 4, 8, 16) and best_q in pm.Q_CANDIDATES
+    assert len(times) == 20 and all(v > 0 for v in times.values())
+    fastest = min(times.values())
+    assert times[(best_s, best_q)] <= 1.02 * fastest + 1e-6
+    props = torch.cuda.get_device_properties(0)
+    key = (props.name, props.multi_processor_count, pm.PM_TUNE_BATCHED, P, 2049, 500)
+    assert pm.tune_lookup(*key) == (best_s, best_q)
+    assert_equal(run_batch(packed, 2048, s=0), want, "tuned s = 0 call")
+    path = str(tmp_path / "tune.json")
+    pm.tune_save(path)
+    pm.tune_clear()
+    assert pm.tune_lookup(*key) == (0, 0)
+    pm.tune_load(path)
+    assert pm.tune_lookup(*key) == (best_s, best_q)
+    # every candidate unit size gives the same words
+    for q in pm.Q_CANDIDATES:
+        pm.tune_clear()
+        pm.tune_load(path)
+        # an entry with this Q for the same size class, then an s = 0 call
+        txt = open(path).read().replace(f'"q": {best_q},', f'"q": {q},')
+        open(path + ".q", "w").write(txt)
+        pm.tune_load(path + ".q")
+        assert pm.tune_lookup(*key) == (best_s, q)
+        assert_equal(run_batch(packed, 2048, s=0), want, f"Q = {q}")
+    pm.tune_clear()

@@ -76,6 +76,39 @@ def test_worst_case_accumulation():
     assert_equal(run((ones, a_off, ones, b_off, c_off), 4095), oracle.polymul(ones, ones, P), "p-1")
 
 
+@pytest.mark.parametrize("deg", [4096, 8191, 16383])
+def test_degrees_beyond_one_k_group(deg):
+    """Pairs whose operands both exceed 4096 terms: each tile is accumulated in K-groups of at
+    most 128 shifts (4096 terms per entry) and the groups' residues added in the epilogue."""
+    packed = inputs.workload_tensor(batch=3, deg=deg, seed=inputs.SEED_BASE + 310 + deg)
+    assert_equal(run(packed, deg), oracle.polymul_batch(*packed[:4], packed[4], P), f"deg {deg}")
+
+
+def test_long_and_short_operands_beyond_4096():
+    """Ragged pairs up to degree 16383: one or both operands beyond one K-group, both orders."""
+    da = np.array([16383, 5000, 16383, 4096, 300, 12000, 0, 9000], np.int64)
+    db = np.array([5000, 16383, 300, 4097, 16383, 12001, 16383, 8999], np.int64)
+    packed = inputs.packed_batch(da, db, 93)
+    assert_equal(run(packed, 16383), oracle.polymul_batch(*packed[:4], packed[4], P))
+
+
+@pytest.mark.parametrize("deg", [8191, 16383])
+def test_worst_case_accumulation_in_k_groups(deg):
+    """Extreme digits at degrees 8191 and 16383: a K-group's sums reach 2^24 exactly, and the groups
+    of a tile are added mod p."""
+    xa, xb = _adversarial_values(P)
+    n = m = deg + 1
+    a = np.full(n, xa, np.uint32)
+    b = np.full(m, xb, np.uint32)
+    a_off = np.array([0, n], np.int64); b_off = np.array([0, m], np.int64)
+    c_off = np.array([0, n + m - 1], np.int64)
+    want = oracle.ntt_polymul(a, b, P)
+    assert_equal(run((a, a_off, b, b_off, c_off), deg), want, "adversarial digits")
+    assert_equal(run((b, b_off, a, a_off, c_off), deg), want, "swapped")
+    k = np.array([0, 4095, 4096, 8191, n - 1, n + m - 2])
+    assert_equal(want[k], [oracle.coeff(a, b, P, int(x)) for x in k], "transform oracle spot check")
+
+
 def test_tensor_workload_full():
     """1024 pairs of degree 4095 against the transform oracle, plus the plain path."""
     packed = inputs.workload_tensor()
