@@ -546,44 +546,63 @@ def measure_rows(pm, torch, dev, flush, clocks, pk, args):
     rows["plain_small"] = {"workload": "degree-1023 pair", "s": s0, "ms": ms0,
                            "macs_per_s": 1024 * 1024 / (ms0 * 1e-3)}
 
-    # --- batched: 4096 pairs, degrees log-uniform in [16, 2048], one graph launch ---
+    # --- batched: 4096 pairs, degrees log-uniform in [16, 2048], one graph launch; (s, Q) by the autotuner ---
     packed = inputs.workload_batched()
     a_data, a_off, b_data, b_off, c_off = packed
-    macs = int(((a_off[1:] - a_off[:-1]) * (b_off[1:] - b_off[:-1])).sum())
+    na_ = a_off[1:] - a_off[:-1]
+    nb_ = b_off[1:] - b_off[:-1]
+    macs = int((na_ * nb_).sum())
     ta = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in packed]
     outb = torch.empty(int(c_off[-1]), dtype=torch.uint32, device=dev)
-    best = None
-    for s in (2, 4, 8):
-        run = lambda s=s: pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_PLAIN,
-                                     s=s, out=outb, total=outb.numel())
-        run()
-        ms = median_ms(run, 10, flush, stream)
-        if best is None or ms < best[1]:
-            best = (s, ms)
-    s_b = best[0]
+    s_b, q_b, tune_b = pm.tune_batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, reps=10, out=outb,
+                                       total=outb.numel())
+    # the model of Section 5 for the batch (Theorem 1 over all pairs' thread-blocks: N = sum of N_s,
+    # the span the longest pair's), in the time unit of one local operation of a block
+    model_b = {}
+    for s in sorted({sv for sv, _ in tune_b}):
+        n_tot, l_max, c_s = 0.0, 0.0, 0.0
+        for n_i, m_i in zip(na_.tolist(), nb_.tolist()):
+            nn_, mm_ = max(n_i, m_i), min(n_i, m_i)
+            if s > mm_:
+                continue
+            pr = pm.model_predict(nn_, mm_, s, 256, 4.0 * rate * SM_MAX_MHZ * 1e6 * SMS / (pk["hbm_gbs"] * 1e9),
+                                  float(SMS))
+            n_tot += pr["N"]
+            l_max = max(l_max, pr["L"])
+            c_s = pr["C"]
+        model_b[s] = (n_tot / SMS + l_max) * c_s * 256 / (rate * SM_MAX_MHZ * 1e6)
+    run_b = lambda: pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_PLAIN, s=0, out=outb,
+                               total=outb.numel())
+    run_b()
+    ms_direct = median_ms(run_b, 20, flush, stream)
     g = torch.cuda.CUDAGraph()
     gs = torch.cuda.Stream()
     with torch.cuda.stream(gs):
-        pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_PLAIN, s=s_b, out=outb,
+        pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_PLAIN, s=0, out=outb,
                    total=outb.numel(), stream=gs)
         gs.synchronize()
         with torch.cuda.graph(g, stream=gs):
-            pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_PLAIN, s=s_b,
+            pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_PLAIN, s=0,
                        out=outb, total=outb.numel(), stream=gs)
     ms_g = median_ms(g.replay, 20, flush, stream)
     want = outb.clone()  # the graph replay's result; the forms below must agree with it
-    # the tensor-core form on the same batch (what PM_AUTO picks for degrees below 4096)
+    # the tensor-core form on the same batch (what PM_AUTO picks for degrees above 2048)
     run_bt = lambda: pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_TENSOR, out=outb,
                                 total=outb.numel())
     run_bt()
     ms_bt = median_ms(run_bt, 10, flush, stream)
     assert torch.equal(outb, want), "batched: tensor and plain forms disagree"
-    rows["batched_plain"] = {"workload": "4096 pairs, degrees log-uniform in [16,2048]", "s": s_b,
+    rows["batched_plain"] = {"workload": "4096 pairs, degrees log-uniform in [16,2048]", "s": s_b, "q": q_b,
                              "form": "warp-level units (degrees below 4096)",
+                             "tuner": "polymul_tune_batched: flushed medians of 10 calls per (s, Q)",
+                             "sweep": [{"s": sv, "q": qv, "ms": ms_, "macs_per_s": macs / (ms_ * 1e-3),
+                                        "model_T_thm_s": model_b.get(sv)}
+                                       for (sv, qv), ms_ in sorted(tune_b.items())],
                              "tensor_form_ms_same_batch": ms_bt,
-                             "macs": macs, "ms_graph": ms_g, "ms_direct": best[1],
+                             "macs": macs, "ms_graph": ms_g, "ms_direct": ms_direct,
                              "macs_per_s": macs / (ms_g * 1e-3), "products_per_s": 4096 / (ms_g * 1e-3),
                              "alu_frac": macs / (ms_g * 1e-3) / alu_peak}
+    del ta, outb, want
 
     # --- the headline batch through the plain CUDA-core form (the comparison the tensor form must win) ---
     tp = inputs.workload_tensor()

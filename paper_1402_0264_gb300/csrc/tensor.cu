@@ -336,19 +336,23 @@ __device__ __forceinline__ void stage_b_8(const uint32_t (&u)[8], uint16_t* dst)
     }
 }
 
-__device__ __forceinline__ void stage_b(const TcTile& tt, uint16_t* sbd, int btid, uint32_t p) {
-    const int nu = 4 * tt.nd + 5;  // positions up to 32 nd + 39, the last one a Hankel row reads
-    for (int u0 = 1 + btid; u0 < nu; u0 += 2 * BLD_THREADS) {
+// Positions [u_lo, u_hi) (groups of 8 digits) of the tile's b digits.  The Hankel
+// rows of slot gi (shifts d_lo + 8 gi .. + nds - 1) read positions
+// 1 + 32 gi .. 32 gi + 4 nds + 4, so the builders stage, before each slot, only
+// the positions it adds: the first slot of a tile waits for 37 positions, not
+// for the whole tile's 4 nd + 4.
+__device__ __forceinline__ void stage_b(const TcTile& tt, uint16_t* sbd, int btid, uint32_t p, int u_lo, int u_hi) {
+    for (int u0 = u_lo + btid; u0 < u_hi; u0 += 2 * BLD_THREADS) {
         const int u1 = u0 + BLD_THREADS;
         uint32_t x0[8], x1[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
             const int g0 = tt.tb0 + 8 * u0 + v - BD_SHIFT, g1 = g0 + 8 * BLD_THREADS;
             x0[v] = (g0 >= 0 && g0 < tt.m) ? (uint32_t)centred(__ldg(tt.b + g0), p) + K_B : K_B;
-            x1[v] = (u1 < nu && g1 >= 0 && g1 < tt.m) ? (uint32_t)centred(__ldg(tt.b + g1), p) + K_B : K_B;
+            x1[v] = (u1 < u_hi && g1 >= 0 && g1 < tt.m) ? (uint32_t)centred(__ldg(tt.b + g1), p) + K_B : K_B;
         }
         stage_b_8(x0, sbd + 8 * u0);
-        if (u1 < nu) stage_b_8(x1, sbd + 8 * u1);
+        if (u1 < u_hi) stage_b_8(x1, sbd + 8 * u1);
     }
 }
 
@@ -569,12 +573,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             wait_parity(bar(BAR_A_FULL + sb), (k >> 1) & 1, WAIT_LIMIT);  // completed: acquires the tile record
             const TcTile tt = s_tiles[sb];
             if (tt.done) break;
-            stage_b(tt, sbd, btid, tp.p);
             const int ngroups = (tt.nd + GROUP_D - 1) / GROUP_D;
             bool stop = false;
+            int u_done = 1;  // b-digit positions staged so far (position 0 is never read)
             for (int gi = 0; gi < ngroups; ++gi, ++G) {
                 const int slot = (int)(G % NH);
-                builders_sync();  // (the b digits are complete before the first slot)
+                // the positions this slot adds (earlier slots' rows never read them, and the
+                // previous tile's rows were all built before the sync that ended its loop)
+                const int u_need = 32 * gi + 4 * min(GROUP_D, tt.nd - gi * GROUP_D) + 5;
+                stage_b(tt, sbd, btid, tp.p, u_done, u_need);
+                u_done = u_need;
+                builders_sync();  // (the slot's b digits are complete before any row reads them)
                 if (btid == 0) {
                     bool st = *s_abort != 0;
                     if (!st && G >= NH && !wait_parity(bar(BAR_H_EMPTY + slot), ((G / NH) - 1) & 1, WL)) {
