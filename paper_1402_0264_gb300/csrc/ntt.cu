@@ -51,6 +51,9 @@ constexpr int NTT_THREADS = 512;
 #ifndef NTT_ROW_MINB
 #define NTT_ROW_MINB 3   // row-pass CTAs per SM the compiler must fit (80 registers, no spills)
 #endif
+#ifndef NTT_COL_MINB
+#define NTT_COL_MINB 2   // column-pass CTAs per SM the compiler must fit (3 would cap at 40 registers and spill)
+#endif
 #ifndef NTT_COLS8_LOG
 #define NTT_COLS8_LOG 11 // column blocks of 8 (not 16) from this log2 N1 on: 64 KiB per CTA, 3 CTAs per SM
 #endif
@@ -214,6 +217,110 @@ __device__ __forceinline__ void bf4(uint32_t& x0, uint32_t& x1, uint32_t& x2, ui
     }
 }
 
+// One radix-2 butterfly with twiddle exponent e (smem_ntt's radix-2 stage).
+template <bool FWD>
+__device__ __forceinline__ void bf2(uint32_t& u, uint32_t& v, const uint2* __restrict__ tw, int e, uint32_t p) {
+    if (FWD) {
+        const uint32_t d = sub_p(u, v, p);
+        u = add_p(u, v, p);
+        v = e ? mul_shoup(d, __ldg(tw + e), p) : d;
+    } else {
+        const uint32_t w = e ? mul_shoup(v, __ldg(tw + e), p) : v;
+        v = sub_p(u, w, p);
+        u = add_p(u, w, p);
+    }
+}
+
+// Column transforms in shared memory by register stages: the levels of
+// smem_ntt (the same butterflies and twiddles, so the same output order),
+// two at a time.  A stage pairs a level of span s_large and radix RL with the
+// next level of span s_small = s_large / RS and radix RS; a thread takes the
+// RS * RL elements base + j + ks s_small + kl s_large (j < s_small) of one
+// column into registers, applies both levels (forward: large span first,
+// inverse: small span first) and writes them back, so each pair of levels
+// costs one read and one write of shared memory.  Columns are side by side,
+// with one pad row after every 16 rows: element n1 of column c is
+// sh[cphys(n1) * COLS + c], cphys(n1) = n1 + n1 / 16, so that the stage whose
+// small span is 1 (16 consecutive rows per unit) reads the units of a warp
+// from distinct banks.
+__device__ __forceinline__ int cphys(int n1) { return n1 + (n1 >> 4); }
+template <bool FWD, int RS, int RL, int COLS>
+__device__ __forceinline__ void col_stage(uint32_t* sh, int logm, int lg_ss, const uint2* __restrict__ tw, uint2 w4,
+                                          uint32_t p) {
+    constexpr int R = RS * RL;
+    const int ss = 1 << lg_ss;
+    const int lg_sl = lg_ss + (RS == 4 ? 2 : 0);
+    const int nunits = COLS << (logm - (RS == 4 ? 2 : 0) - (RL == 4 ? 2 : 1));
+    for (int u = threadIdx.x; u < nunits; u += blockDim.x) {
+        const int c = u & (COLS - 1), v = u / COLS;
+        const int j = v & (ss - 1), blk = v >> lg_ss;
+        const int base = (blk << (lg_sl + (RL == 4 ? 2 : 1))) + j;
+        uint32_t r[R];
+#pragma unroll
+        for (int kl = 0; kl < RL; ++kl)
+#pragma unroll
+            for (int ks = 0; ks < RS; ++ks) r[ks + RS * kl] = sh[cphys(base + (ks << lg_ss) + (kl << lg_sl)) * COLS + c];
+        // the level of span s_large: offsets j + ks s_small in its blocks
+        auto large = [&]() {
+#pragma unroll
+            for (int ks = 0; ks < RS; ++ks) {
+                const int jl = j + (ks << lg_ss);
+                if (RL == 4) {
+                    const int e = jl << (logm - 2 - lg_sl);
+                    bf4<FWD>(r[ks], r[ks + RS], r[ks + 2 * RS], r[ks + 3 * RS], w4, tw, e, p);
+                } else {
+                    bf2<FWD>(r[ks], r[ks + RS], tw, jl, p);  // span M/2: twiddle exponent = offset
+                }
+            }
+        };
+        // the level of span s_small (radix 4): offset j in its blocks
+        auto small = [&]() {
+            if (RS == 4) {
+                const int e = j << (logm - 2 - lg_ss);
+#pragma unroll
+                for (int kl = 0; kl < RL; ++kl) bf4<FWD>(r[RS * kl], r[RS * kl + 1], r[RS * kl + 2], r[RS * kl + 3], w4, tw, e, p);
+            }
+        };
+        if (FWD) { large(); small(); } else { small(); large(); }
+#pragma unroll
+        for (int kl = 0; kl < RL; ++kl)
+#pragma unroll
+            for (int ks = 0; ks < RS; ++ks) sh[cphys(base + (ks << lg_ss) + (kl << lg_sl)) * COLS + c] = r[ks + RS * kl];
+    }
+    __syncthreads();
+}
+
+// The transforms of COLS side-by-side columns of length M = 2^logm (1 <= logm):
+// levels in the order of smem_ntt (forward: radix 2 at span M/2 if logm is odd,
+// then radix 4 from span M/4 or M/8 down to 1; inverse: the reverse), taken two
+// at a time.
+template <bool FWD, int COLS>
+__device__ void col_transform(uint32_t* sh, int logm, const uint2* __restrict__ tw, uint32_t p) {
+    const uint2 w4 = logm >= 2 ? __ldg(tw + (1 << (logm - 2))) : make_uint2(0, 0);
+    const int odd = logm & 1, n4 = logm >> 1;  // levels: odd radix-2, n4 radix-4
+    const int nlev = odd + n4;
+    // level i of the forward order: span log2 (logm - 1 for the radix-2 level), radix
+    auto lv_lg = [&](int i) { return odd ? (i == 0 ? logm - 1 : logm - 1 - 2 * i) : logm - 2 - 2 * i; };
+    auto lv_r2 = [&](int i) { return odd && i == 0; };
+    for (int st = 0; st < nlev; st += 2) {
+        // the forward order takes levels st, st + 1; the inverse the mirror ones
+        const int a = FWD ? st : nlev - 1 - st;   // first level executed
+        const int b = FWD ? st + 1 : nlev - 2 - st;
+        if (st + 1 < nlev) {
+            const int large = FWD ? a : b, small = FWD ? b : a;
+            if (lv_r2(large))
+                col_stage<FWD, 4, 2, COLS>(sh, logm, lv_lg(small), tw, w4, p);
+            else
+                col_stage<FWD, 4, 4, COLS>(sh, logm, lv_lg(small), tw, w4, p);
+        } else {
+            if (lv_r2(a))
+                col_stage<FWD, 1, 2, COLS>(sh, logm, lv_lg(a), tw, w4, p);
+            else
+                col_stage<FWD, 1, 4, COLS>(sh, logm, lv_lg(a), tw, w4, p);
+        }
+    }
+}
+
 // A length-4096 transform as three radix-16 stages, each two radix-4 levels
 // done in registers by 256 threads holding 16 elements (the levels of
 // smem_ntt with logm = 12, grouped by the elements they touch):
@@ -254,6 +361,69 @@ __device__ __forceinline__ void row_stage(int stage, uint32_t (&r)[16], uint2 w4
     }
 }
 
+// A radix-4 butterfly with the twiddles given (tw1..tw3 = w^e, w^2e, w^3e; none when !on).
+template <bool FWD>
+__device__ __forceinline__ void bf4t(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint2 w4, uint2 tw1,
+                                     uint2 tw2, uint2 tw3, bool on, uint32_t p) {
+    if (!FWD && on) {
+        x1 = mul_shoup(x1, tw1, p);
+        x2 = mul_shoup(x2, tw2, p);
+        x3 = mul_shoup(x3, tw3, p);
+    }
+    const uint32_t t0 = add_p(x0, x2, p), t1 = sub_p(x0, x2, p);
+    const uint32_t t2 = add_p(x1, x3, p), t3 = mul_shoup(sub_p(x1, x3, p), w4, p);
+    x0 = add_p(t0, t2, p);
+    x2 = sub_p(t0, t2, p);
+    x1 = add_p(t1, t3, p);
+    x3 = sub_p(t1, t3, p);
+    if (FWD && on) {
+        x1 = mul_shoup(x1, tw1, p);
+        x2 = mul_shoup(x2, tw2, p);
+        x3 = mul_shoup(x3, tw3, p);
+    }
+}
+
+// row_stage on NR arrays at once (the forward transforms of a's and b's rows): every
+// twiddle is loaded once for all of them; stage 3's come from the kernel parameters.
+template <bool FWD, int NR>
+__device__ __forceinline__ void row_stage_n(int stage, uint32_t (*rs[NR])[16], uint2 w4, const uint2* __restrict__ tw,
+                                            const uint2 (&c3)[3][3], uint32_t p) {
+    const int t = threadIdx.x, tp = t & 15;
+    auto lvA = [&]() {
+#pragma unroll
+        for (int l0 = 0; l0 < 4; ++l0) {
+            uint2 a1, a2, a3;
+            bool on = true;
+            if (stage == 3) {
+                on = l0 != 0;
+                a1 = c3[l0 ? l0 - 1 : 0][0]; a2 = c3[l0 ? l0 - 1 : 0][1]; a3 = c3[l0 ? l0 - 1 : 0][2];
+            } else {
+                const int e = stage == 1 ? t + 256 * l0 : 16 * (tp + 16 * l0);
+                on = e != 0;
+                a1 = __ldg(tw + e); a2 = __ldg(tw + 2 * e); a3 = __ldg(tw + 3 * e);
+            }
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                uint32_t (&r)[16] = *rs[k];
+                bf4t<FWD>(r[l0], r[l0 + 4], r[l0 + 8], r[l0 + 12], w4, a1, a2, a3, on, p);
+            }
+        }
+    };
+    auto lvB = [&]() {
+        const int e = stage == 1 ? 4 * t : stage == 2 ? 64 * tp : 0;
+        uint2 a1 = make_uint2(0, 0), a2 = a1, a3 = a1;
+        if (e) { a1 = __ldg(tw + e); a2 = __ldg(tw + 2 * e); a3 = __ldg(tw + 3 * e); }
+#pragma unroll
+        for (int l1 = 0; l1 < 4; ++l1)
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                uint32_t (&r)[16] = *rs[k];
+                bf4t<FWD>(r[4 * l1], r[4 * l1 + 1], r[4 * l1 + 2], r[4 * l1 + 3], w4, a1, a2, a3, e != 0, p);
+            }
+    };
+    if (FWD) { lvA(); lvB(); } else { lvB(); lvA(); }
+}
+
 // element index of register l of thread t in stage `stage`
 __device__ __forceinline__ int row_index(int stage, int t, int l) {
     return stage == 1 ? t + 256 * l : stage == 2 ? 256 * (t >> 4) + (t & 15) + 16 * l : 16 * t + l;
@@ -266,6 +436,9 @@ struct NttTables {
     const uint2 *hi, *ihi;    // w_N^(4096 f), w_N^(-4096 f), f < N1 (= w_N1^f)
     uint2 scale;              // N^-1 2^32 mod p
     uint32_t w4_unused;
+    // the twiddles of the row transforms' third stage, the same for every thread:
+    // st3[l0 - 1][k - 1] = w_N2^(256 l0 k) (ist3: w_N2^-(256 l0 k)), l0, k = 1..3
+    uint2 st3[3][3], ist3[3][3];
 };
 
 // x * w_N^e (or w_N^-e) with e < N: w_N^e = lo[e mod 4096] * hi[e / 4096].
@@ -305,7 +478,7 @@ __device__ __forceinline__ void cp_async4_ntt(uint32_t* dst, const uint32_t* src
 // ([n1][cols]), so loads and stores touch 4*cols contiguous bytes per row and
 // the butterflies of the `cols` columns run side by side.
 template <int COLS>
-__global__ void __launch_bounds__(NTT_THREADS) ntt_col_fwd_kernel(
+__global__ void __launch_bounds__(NTT_THREADS, NTT_COL_MINB) ntt_col_fwd_kernel(
     const uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ b, int m,
     uint32_t* __restrict__ ta, uint32_t* __restrict__ tb_out, int logn1, NttTables tb, NttMod md) {
     constexpr int cols = COLS;
@@ -318,18 +491,18 @@ __global__ void __launch_bounds__(NTT_THREADS) ntt_col_fwd_kernel(
     for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
         const int j = idx % cols, n1 = idx / cols;
         const int g = n1 * NTT_N2 + c0 + j;
-        cp_async4_ntt(sh + idx, x + (g < len ? g : 0), g < len);
+        cp_async4_ntt(sh + cphys(n1) * cols + j, x + (g < len ? g : 0), g < len);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    smem_ntt<true, COLS>(sh, cols, 1, cols, true, logn1, tb.hi, md.p);
+    col_transform<true, COLS>(sh, logn1, tb.hi, md.p);
     const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
     for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
         const int j = idx % cols, pos = idx / cols;
         const uint32_t k1 = freq_of_pos_fast((uint32_t)pos, logn1);
         const uint32_t e = (uint32_t)(((uint64_t)(c0 + j) * k1) & nmask);
-        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root(sh[idx], e, tb.lo, tb.hi, md.p);
+        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root(sh[cphys(pos) * cols + j], e, tb.lo, tb.hi, md.p);
     }
 }
 
@@ -350,8 +523,9 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
         r[l] = ta[r0 + t + 256 * l];
         q[l] = tbuf[r0 + t + 256 * l];
     }
-    row_stage<true>(1, r, w4, tb.row, p);
-    row_stage<true>(1, q, w4, tb.row, p);
+    uint32_t (*rq[2])[16] = {&r, &q};
+    uint32_t (*ro[1])[16] = {&r};
+    row_stage_n<true, 2>(1, rq, w4, tb.row, tb.st3, p);
 #pragma unroll
     for (int l = 0; l < 16; ++l) {
         sA[rphys(t + 256 * l)] = r[l];
@@ -363,8 +537,7 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
         r[l] = sA[rphys(row_index(2, t, l))];
         q[l] = sB[rphys(row_index(2, t, l))];
     }
-    row_stage<true>(2, r, w4, tb.row, p);
-    row_stage<true>(2, q, w4, tb.row, p);
+    row_stage_n<true, 2>(2, rq, w4, tb.row, tb.st3, p);
 #pragma unroll
     for (int l = 0; l < 16; ++l) {
         sA[rphys(row_index(2, t, l))] = r[l];
@@ -377,25 +550,24 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
         r[l] = sA[rphys(16 * t + l)];
         q[l] = sB[rphys(16 * t + l)];
     }
-    row_stage<true>(3, r, w4, tb.row, p);
-    row_stage<true>(3, q, w4, tb.row, p);
+    row_stage_n<true, 2>(3, rq, w4, tb.row, tb.st3, p);
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[l] = mul_mont(r[l], q[l], md);
-    row_stage<false>(3, r, iw4, tb.irow, p);
+    row_stage_n<false, 1>(3, ro, iw4, tb.irow, tb.ist3, p);
     __syncthreads();  // every thread has read its stage-3 inputs from sA
 #pragma unroll
     for (int l = 0; l < 16; ++l) sA[rphys(16 * t + l)] = r[l];
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[l] = sA[rphys(row_index(2, t, l))];
-    row_stage<false>(2, r, iw4, tb.irow, p);
+    row_stage_n<false, 1>(2, ro, iw4, tb.irow, tb.ist3, p);
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < 16; ++l) sA[rphys(row_index(2, t, l))] = r[l];
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[l] = sA[rphys(t + 256 * l)];
-    row_stage<false>(1, r, iw4, tb.irow, p);
+    row_stage_n<false, 1>(1, ro, iw4, tb.irow, tb.ist3, p);
     const uint32_t k1 = freq_of_pos_fast(blockIdx.x, logn1);
     const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
 #pragma unroll
@@ -408,7 +580,7 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
 
 // ---- four-step pass 3: inverse column transforms, scale, store ----
 template <int COLS>
-__global__ void __launch_bounds__(NTT_THREADS) ntt_col_inv_kernel(const uint32_t* __restrict__ ta,
+__global__ void __launch_bounds__(NTT_THREADS, NTT_COL_MINB) ntt_col_inv_kernel(const uint32_t* __restrict__ ta,
                                                                   uint32_t* __restrict__ c, int L,
                                                                   int logn1, NttTables tb, NttMod md) {
     constexpr int cols = COLS;
@@ -417,16 +589,16 @@ __global__ void __launch_bounds__(NTT_THREADS) ntt_col_inv_kernel(const uint32_t
     const int c0 = blockIdx.x * cols;
     for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
         const int j = idx % cols, pos = idx / cols;
-        cp_async4_ntt(sh + idx, ta + (size_t)pos * NTT_N2 + c0 + j, true);
+        cp_async4_ntt(sh + cphys(pos) * cols + j, ta + (size_t)pos * NTT_N2 + c0 + j, true);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    smem_ntt<false, COLS>(sh, cols, 1, cols, true, logn1, tb.ihi, md.p);
+    col_transform<false, COLS>(sh, logn1, tb.ihi, md.p);
     for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
         const int j = idx % cols, n1 = idx / cols;
         const int64_t g = (int64_t)n1 * NTT_N2 + c0 + j;
-        if (g < L) c[g] = mul_shoup(sh[idx], tb.scale, md.p);
+        if (g < L) c[g] = mul_shoup(sh[cphys(n1) * cols + j], tb.scale, md.p);
     }
 }
 
@@ -509,6 +681,14 @@ static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStrea
     const uint32_t ninv = powmod_h(N % p, p - 2, p);
     const uint32_t r32 = (uint32_t)((1ull << 32) % p);
     ts.t.scale = shoup_pair((uint32_t)((uint64_t)ninv * r32 % p), p);
+    if (logn > NTT_N2_LOG) {
+        const uint32_t w2 = powmod_h(w, (uint64_t)n1, p), w2i = powmod_h(wi, (uint64_t)n1, p);  // w_N2, w_N2^-1
+        for (int l0 = 1; l0 <= 3; ++l0)
+            for (int k = 1; k <= 3; ++k) {
+                ts.t.st3[l0 - 1][k - 1] = shoup_pair(powmod_h(w2, (uint64_t)(256 * l0 * k), p), p);
+                ts.t.ist3[l0 - 1][k - 1] = shoup_pair(powmod_h(w2i, (uint64_t)(256 * l0 * k), p), p);
+            }
+    }
     g_tables[key] = ts;
     *out = ts.t;
     return PM_OK;
@@ -567,10 +747,13 @@ pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m,
     uint32_t* ta = reinterpret_cast<uint32_t*>(sc->ntt);
     uint32_t* tbuf = ta + N;
     const int cols = logn1 >= NTT_COLS8_LOG ? 8 : 16;  // a CTA's columns: cols * N1 words of shared memory
-    const size_t col_smem = sizeof(uint32_t) * (size_t)cols * ((size_t)1 << logn1);
+    const size_t col_rows = ((size_t)1 << logn1) + ((size_t)1 << logn1) / 16;  // with a pad row per 16
+    const size_t col_smem = sizeof(uint32_t) * (size_t)cols * col_rows;
     static int col_done[64] = {};
     if (!col_done[ws->device]) {
-        const int mx = (int)(sizeof(uint32_t) * 16 * (1 << (NTT_MAX_LOG - NTT_N2_LOG - 1)));
+        // the largest block: 8 columns of N1 = 2^(NTT_MAX_LOG - 12) rows with their pad rows
+        const int n1max = 1 << (NTT_MAX_LOG - NTT_N2_LOG);
+        const int mx = (int)(sizeof(uint32_t) * 8 * (n1max + n1max / 16));
         const void* ks[4] = {(const void*)ntt_col_fwd_kernel<8>, (const void*)ntt_col_fwd_kernel<16>,
                              (const void*)ntt_col_inv_kernel<8>, (const void*)ntt_col_inv_kernel<16>};
         for (const void* k : ks) {
