@@ -146,6 +146,36 @@ pm_status ensure_scratch(void** buf, size_t* have, size_t bytes, cudaStream_t st
     return PM_OK;
 }
 
+// ---- checked build: the inputs' words must be below p (Section 3's field Z/pZ) ----
+#ifdef POLYMUL_CHECKED
+// Sets PM_ERR_RANGE in the status word if a word of x[0 .. len) is >= p; len is
+// *len_dev when len_dev is given (a CSR batch's total, read on the device).
+__global__ void chk_range_kernel(const uint32_t* __restrict__ x, int64_t len, const int64_t* __restrict__ len_dev,
+                                 uint32_t p, int* status) {
+    const int64_t n = len_dev ? *len_dev : len;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (x[i] >= p) {
+            atomicCAS(status, 0, (int)PM_ERR_RANGE);
+            return;
+        }
+}
+#endif
+
+// Checked build: scans an input on `stream` (stream-ordered, before the product's
+// launches); a no-op otherwise.
+static pm_status chk_input(const uint32_t* x, int64_t len, const int64_t* len_dev, uint32_t p, void* stream,
+                           DeviceWorkspace* ws) {
+#ifdef POLYMUL_CHECKED
+    chk_range_kernel<<<4 * ws->num_sms, 256, 0, (cudaStream_t)stream>>>(x, len, len_dev, p, ws->status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(1);
+#else
+    (void)x; (void)len; (void)len_dev; (void)p; (void)stream; (void)ws;
+#endif
+    return PM_OK;
+}
+
 // ---- the block parameter an s = 0 call takes: the tuned one, else a default ----
 static int default_s(int64_t n, int64_t m, uint32_t p) {
     TuneChoice tc;
@@ -211,6 +241,8 @@ pm_status polymul_plain(const uint32_t* a, int64_t deg_a, const uint32_t* b, int
     if (s == 0) s = default_s(deg_a + 1, deg_b + 1, p);
     DeviceWorkspace* ws = workspace(stream, &rc);
     if (!ws) return rc;
+    if ((rc = chk_input(a, deg_a + 1, nullptr, p, stream, ws)) != PM_OK) return rc;
+    if ((rc = chk_input(b, deg_b + 1, nullptr, p, stream, ws)) != PM_OK) return rc;
     return launch_plain(a, deg_a + 1, b, deg_b + 1, c, p, s, (cudaStream_t)stream, ws);
 }
 
@@ -222,6 +254,8 @@ pm_status polymul_plain_ell(const uint32_t* a, int64_t deg_a, const uint32_t* b,
     if (ell != 128 && ell != 256 && ell != 512) return PM_ERR_INVALID_ARG;
     DeviceWorkspace* ws = workspace(stream, &rc);
     if (!ws) return rc;
+    if ((rc = chk_input(a, deg_a + 1, nullptr, p, stream, ws)) != PM_OK) return rc;
+    if ((rc = chk_input(b, deg_b + 1, nullptr, p, stream, ws)) != PM_OK) return rc;
     return launch_plain_ell(a, deg_a + 1, b, deg_b + 1, c, p, s, ell, (cudaStream_t)stream, ws);
 }
 
@@ -231,6 +265,8 @@ pm_status polymul_ntt(const uint32_t* a, int64_t deg_a, const uint32_t* b, int64
     if (rc != PM_OK) return rc;
     DeviceWorkspace* ws = workspace(stream, &rc);
     if (!ws) return rc;
+    if ((rc = chk_input(a, deg_a + 1, nullptr, p, stream, ws)) != PM_OK) return rc;
+    if ((rc = chk_input(b, deg_b + 1, nullptr, p, stream, ws)) != PM_OK) return rc;
     return launch_ntt(a, deg_a + 1, b, deg_b + 1, c, p, g, (cudaStream_t)stream, ws);
 }
 
@@ -249,6 +285,8 @@ pm_status polymul_divide(const uint32_t* a, int64_t deg_a, const uint32_t* b, in
     pm_status rc = PM_OK;
     DeviceWorkspace* ws = workspace(stream, &rc);
     if (!ws) return rc;
+    if ((rc = chk_input(a, deg_a + 1, nullptr, p, stream, ws)) != PM_OK) return rc;
+    if ((rc = chk_input(b, deg_b + 1, nullptr, p, stream, ws)) != PM_OK) return rc;
     return launch_divide(a, deg_a + 1, b, deg_b + 1, q, r, p, s, (cudaStream_t)stream, ws);
 }
 
@@ -285,6 +323,10 @@ pm_status polymul_batched(int64_t batch, const uint32_t* a_data, const int64_t* 
     pm_status rc = PM_OK;
     DeviceWorkspace* ws = workspace(stream, &rc);
     if (!ws) return rc;
+    // (the words of every pair: a_data[0 .. a_off[batch]) when the offsets are valid; a bad
+    // layout is reported by the planners)
+    if ((rc = chk_input(a_data, 0, a_off + batch, p, stream, ws)) != PM_OK) return rc;
+    if ((rc = chk_input(b_data, 0, b_off + batch, p, stream, ws)) != PM_OK) return rc;
     // PM_AUTO: the tensor cores for batches with degrees above 2048; below, the
     // warp-level plain form measured faster (4096 pairs of degrees in [16, 2048]:
     // 0.19 ms against 0.21 ms)

@@ -68,6 +68,27 @@ __device__ __forceinline__ uint32_t barrett(uint64_t x, uint32_t p, uint64_t mu)
 }
 
 // ---------------------------------------------------------------------------
+// The checked build (compiled with -DPOLYMUL_CHECKED into a library of its
+// own; compute-sanitizer is not available to every user of this code).
+// PM_CHK(cond) guards a global or shared-memory access: when cond fails it
+// records PM_ERR_INTERNAL in the device status word and returns false, so the
+// caller skips the access instead of faulting; in the normal build it is the
+// constant true and costs nothing.  Each translation unit keeps the status
+// word's address in a constant of its own, bound by chk_bind before its
+// launches.
+// ---------------------------------------------------------------------------
+#ifdef POLYMUL_CHECKED
+static __constant__ int* g_chk_status;
+__device__ __forceinline__ bool pm_chk(bool ok) {
+    if (!ok && g_chk_status) atomicCAS(g_chk_status, 0, (int)PM_ERR_INTERNAL);
+    return ok;
+}
+#define PM_CHK(cond) pm_chk(cond)
+#else
+#define PM_CHK(cond) true
+#endif
+
+// ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
 ModParams host_mod_params(uint32_t p, int kb);
@@ -112,6 +133,23 @@ pm_status stream_scratch(DeviceWorkspace* ws, cudaStream_t st, StreamScratch** o
 pm_status ensure_scratch(void** buf, size_t* have, size_t bytes, cudaStream_t st, bool zero);
 
 pm_status cuda_fail(cudaError_t e);
+
+// Checked build: points this translation unit's status constant at the device's
+// status word (once per device); a no-op otherwise.
+static inline cudaError_t chk_bind(DeviceWorkspace* ws) {
+#ifdef POLYMUL_CHECKED
+    static int bound[64] = {};
+    if (ws->device >= 0 && ws->device < 64 && !bound[ws->device]) {
+        cudaError_t e = cudaMemcpyToSymbol(g_chk_status, &ws->status, sizeof(int*));
+        if (e != cudaSuccess) return e;
+        bound[ws->device] = 1;
+    }
+#else
+    (void)ws;
+#endif
+    return cudaSuccess;
+}
+
 // cudaMalloc, unless a test has asked for the next allocations to fail
 // (polymul_debug_set(PM_DEBUG_FAIL_ALLOC, k)).
 cudaError_t dev_alloc(void** ptr, size_t bytes);

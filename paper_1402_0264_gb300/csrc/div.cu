@@ -94,6 +94,8 @@ __global__ void __launch_bounds__(DIV_THREADS) div_round_kernel(uint32_t* __rest
     __shared__ uint32_t bhq[DIV_SMAX];           // its Shoup quotients floor(bh 2^32 / p)
     __shared__ uint32_t sq[DIV_SMAX];            // the round's quotient coefficients
     __shared__ uint32_t sb[DIV_BODY + DIV_SMAX]; // b window of the body
+    // (uniform: before any barrier) the round's steps and the body window fit the shared arrays
+    if (!PM_CHK(s >= 1 && s <= DIV_SMAX && blockDim.x == DIV_THREADS)) return;
     const uint32_t w = inv[0], wq = inv[1];
     if (w == 0) return;  // b's leading coefficient has no inverse (status set by the setup)
     const int tid = threadIdx.x;
@@ -179,6 +181,8 @@ pm_status launch_divide(const uint32_t* a, int64_t n, const uint32_t* b, int64_t
     uint32_t* work = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(sc->div) + 256);
     const int64_t d_b = m - 1;
     const int setup_blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)ws->num_sms);
+    cudaError_t eb = chk_bind(ws);
+    if (eb != cudaSuccess) return cuda_fail(eb);
     div_setup_kernel<<<setup_blocks, 256, 0, st>>>(a, n, b, d_b, p, work, inv, ws->status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);

@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(GCD_THREADS, 1) gcd_round_kernel(
     __shared__ int r_k, r_ua, r_ub, r_kind;
     __shared__ int64_t r_dg;
 
+    // (uniform: before any barrier) the heads, step records and windows fit their arrays
+    if (!PM_CHK(H <= GCD_HMAX && s <= GCD_SMAX && GCD_T + 2 * H <= GCD_WMAX && blockDim.x == GCD_THREADS)) return;
     const GcdState s0 = *sin;
     const int tid = threadIdx.x;
     if (s0.done) {
@@ -201,7 +203,9 @@ __global__ void __launch_bounds__(GCD_THREADS, 1) gcd_round_kernel(
             const int vr_new = min(min(vr, ur + vd - ud), ur + (s - k) + GCD_HEXTRA);
             // the next 32 entries first: the new leading coefficient is the first nonzero one
             const int i0h = ur + 1 + lane;
-            const bool live = i0h < vr_new;
+            // (entries below vr_new of r and below vr_new + sh of d: within the heads)
+            const bool hok = PM_CHK(vr_new <= GCD_HMAX && vr_new + sh <= GCD_HMAX);
+            const bool live = hok && i0h < vr_new;
             uint32_t v = gcd_comb<MONT>(c1, hAB[offr + (live ? i0h : 0)], c2n, hAB[offd + (live ? i0h + sh : 0)], md);
             v = live ? v : 0u;
             if (live) hAB[offr + i0h] = v;
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(GCD_THREADS, 1) gcd_round_kernel(
             const int f = __ffs(msk) - 1;
             uint32_t lnew = __shfl_sync(0xffffffffu, v, f < 0 ? 0 : f);
 #pragma unroll 4
-            for (int i = i0h + 32; i < vr_new; i += 32)
+            for (int i = i0h + 32; hok && i < vr_new; i += 32)
                 hAB[offr + i] = gcd_comb<MONT>(c1, hAB[offr + i], c2n, hAB[offd + i + sh], md);
             if (lane == 0) {
                 rc1[k] = c1;
@@ -404,6 +408,8 @@ pm_status launch_gcd(const uint32_t* a, int64_t na, const uint32_t* b, int64_t n
     uint64_t launches = 0;
 
     const int init_blocks = (int)std::min<int64_t>((nmax + 255) / 256, 4 * (int64_t)ws->num_sms);
+    cudaError_t eb = chk_bind(ws);
+    if (eb != cudaSuccess) return cuda_fail(eb);
     gcd_init_kernel<<<init_blocks, 256, 0, st>>>(a, na, b, nb, A[0], B[0], p, state);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);

@@ -255,6 +255,7 @@ __device__ __forceinline__ void col_stage(uint32_t* sh, int logm, int lg_ss, con
         const int c = u & (COLS - 1), v = u / COLS;
         const int j = v & (ss - 1), blk = v >> lg_ss;
         const int base = (blk << (lg_sl + (RL == 4 ? 2 : 1))) + j;
+        if (!PM_CHK(base + ((RS - 1) << lg_ss) + ((RL - 1) << lg_sl) < (1 << logm))) continue;
         uint32_t r[R];
 #pragma unroll
         for (int kl = 0; kl < RL; ++kl)
@@ -484,6 +485,7 @@ __global__ void __launch_bounds__(NTT_THREADS, NTT_COL_MINB) ntt_col_fwd_kernel(
     constexpr int cols = COLS;
     extern __shared__ uint32_t sh[];
     const int N1 = 1 << logn1;
+    if (!PM_CHK((blockIdx.x + 1) * cols <= NTT_N2 && blockIdx.y < 2)) return;  // (uniform: before any barrier)
     const uint32_t* x = blockIdx.y == 0 ? a : b;
     const int len = blockIdx.y == 0 ? n : m;
     uint32_t* out = blockIdx.y == 0 ? ta : tb_out;
@@ -514,6 +516,7 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
     __shared__ uint32_t sB[ROW_WORDS];
     const int t = threadIdx.x;
     const size_t r0 = (size_t)blockIdx.x * NTT_N2;
+    if (!PM_CHK(blockIdx.x < (1u << logn1) && blockDim.x == 256)) return;  // (uniform: before any barrier)
     const uint32_t p = md.p;
     const uint2 w4 = __ldg(tb.row + NTT_N2 / 4), iw4 = __ldg(tb.irow + NTT_N2 / 4);
     uint32_t r[16], q[16];
@@ -587,6 +590,7 @@ __global__ void __launch_bounds__(NTT_THREADS, NTT_COL_MINB) ntt_col_inv_kernel(
     extern __shared__ uint32_t sh[];
     const int N1 = 1 << logn1;
     const int c0 = blockIdx.x * cols;
+    if (!PM_CHK((blockIdx.x + 1) * cols <= NTT_N2)) return;  // (uniform: before any barrier)
     for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
         const int j = idx % cols, pos = idx / cols;
         cp_async4_ntt(sh + cphys(pos) * cols + j, ta + (size_t)pos * NTT_N2 + c0 + j, true);
@@ -716,6 +720,8 @@ pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m,
     NttTables tb;
     pm_status rc = get_tables(ws->device, p, g, logn, st, &tb);
     if (rc != PM_OK) return rc;
+    cudaError_t eb = chk_bind(ws);
+    if (eb != cudaSuccess) return cuda_fail(eb);
     NttMod md;
     md.p = p;
     uint32_t inv = 1;  // p^-1 mod 2^32 by Newton iteration (p odd)

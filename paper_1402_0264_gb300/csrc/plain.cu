@@ -127,23 +127,24 @@ __device__ __forceinline__ ChunkDims chunk_dims(int jb0, int jb1, int ci, int f)
 // Issues the copies of one chunk: b[jc .. jc+clen) (zeros up to CL) and the
 // a-window a[d0-(jc+CL-1) .. d0+TD-jc) (zeros outside [0, n)), by threads
 // tid, tid + nthr, ... of the group that stages (AW = a-window words).
-template <int S, int AW>
+template <int S, int AW, int CH = CHUNK_MAX>
 __device__ __forceinline__ void stage_chunk(const uint32_t* __restrict__ a, int n,
-                                            const uint32_t* __restrict__ b, int d0,
+                                            const uint32_t* __restrict__ b, int m, int d0,
                                             const ChunkDims& ch, uint32_t* buf, int tid, int nthr) {
     using C = Cfg<S>;
     uint32_t* sA = buf;
     uint32_t* sB = buf + AW;
     for (int i = tid; i < ch.CL; i += nthr) {
         const bool v = i < ch.clen;
-        cp_async4(sB + i, b + (v ? ch.jc + i : 0), v);
+        if (PM_CHK(i < CH && (!v || (ch.jc + i >= 0 && ch.jc + i < m))))
+            cp_async4(sB + i, b + (v ? ch.jc + i : 0), v);
     }
     const int abase = d0 - (ch.jc + ch.CL - 1);
     const int alen = C::TD + ch.CL - 1;
     for (int i = tid; i < alen; i += nthr) {
         const int ai = abase + i;
         const bool v = ai >= 0 && ai < n;
-        cp_async4(sA + a_phys(FRONT + i), a + (v ? ai : 0), v);
+        if (PM_CHK(a_phys(FRONT + i) < AW)) cp_async4(sA + a_phys(FRONT + i), a + (v ? ai : 0), v);
     }
     cp_async_commit();
 }
@@ -171,7 +172,7 @@ __device__ __forceinline__ void load_group(const uint32_t* sA, int base, uint32_
 // d = d0 + S*lane + e, over the share of warp `warp` of the nw warps that
 // split the chunk.  Values stay congruent mod p and below 2^64 (see
 // ModParams); fold_ctr counts sub-steps since the last fold.
-template <int S>
+template <int S, int AW = Cfg<S>::A_WORDS, int CH = CHUNK_MAX>
 __device__ __forceinline__ void compute_chunk(const uint32_t* sA, const uint32_t* sB, int CL,
                                               const ModParams& mp, uint64_t (&acc)[S], int& fold_ctr,
                                               int warp, int nw) {
@@ -182,6 +183,11 @@ __device__ __forceinline__ void compute_chunk(const uint32_t* sA, const uint32_t
     const int nsub = qw + (warp < rw ? 1 : 0);
     const int r0 = KB * (warp * qw + min(warp, rw));
     int base = S * lane + CL - KB - r0;  // window index of group 0 at the current sub-step
+    // the window words this thread reads run from base - nsub KB (the last prefetch) to
+    // base + NGW KB - 1, the b words from r0 to r0 + nsub KB - 1
+    if (!PM_CHK(FRONT + base - nsub * KB >= 0 && a_phys(FRONT + base + NGW * KB - 1) < AW &&
+                r0 + nsub * KB <= CH))
+        return;
     uint32_t ring[R][KB];
 #pragma unroll
     for (int g = 0; g < NGW; ++g) load_group<S>(sA, base + g * KB, ring[(R - g) % R]);
@@ -293,6 +299,7 @@ __host__ __device__ __forceinline__ int64_t cum_len(int64_t n, int64_t m, int64_
 }
 
 constexpr int64_t MIN_POSITIONS = 64;  // smallest share of a CTA (positions of TD MACs each)
+constexpr int64_t COUNTER_REGION_DEV = 32768;  // tile counters at the start of the scratch (COUNTER_REGION)
 
 // Scratch of one launch: 2 partial-sum slots of TD words per CTA and one
 // counter per CTA (zero between calls).
@@ -396,6 +403,9 @@ __device__ __forceinline__ void finish_segment(const Seg& sg, uint64_t (&acc)[S]
     }
     const int64_t k1 = sp.owner(sg.s_tile), k2 = sp.owner(sg.e_tile - 1);
     const int64_t slot = 2 * k + (sg.x == x0 ? 0 : 1);
+    // (the scratch holds 2 slots per launched CTA and COUNTER_REGION counters)
+    if (!PM_CHK(slot < 2 * (int64_t)gridDim.x && k1 >= 0 && k2 < (int64_t)gridDim.x && k1 < COUNTER_REGION_DEV))
+        return;
     uint32_t* mine = sk.slots + slot * C::TD;
     for (int o = threadIdx.x; o < C::TD; o += NTW) mine[o] = sm.red[o];
     __syncthreads();
@@ -478,8 +488,8 @@ __global__ void PM_BOUNDS(W) plain_sk_kernel(
         cur.f = FIRST_CHUNK;
         cur.nchunks = 1 + (cur.jb1 - cur.jb0 - FIRST_CHUNK + CHUNK_MAX - 1) / CHUNK_MAX;
     }
-    stage_chunk<S, C::A_WORDS>(cur.a, cur.n, cur.b, cur.d0, chunk_dims<KB>(cur.jb0, cur.jb1, 0, cur.f), sm.buf,
-                               threadIdx.x, NTW);
+    stage_chunk<S, C::A_WORDS>(cur.a, cur.n, cur.b, cur.m, cur.d0, chunk_dims<KB>(cur.jb0, cur.jb1, 0, cur.f),
+                               sm.buf, threadIdx.x, NTW);
     for (;;) {
         Seg nxt = cur;
         int nci = ci + 1;
@@ -494,8 +504,9 @@ __global__ void PM_BOUNDS(W) plain_sk_kernel(
             }
         }
         if (has_next) {  // the next chunk streams in while this one is used
-            stage_chunk<S, C::A_WORDS>(nxt.a, nxt.n, nxt.b, nxt.d0, chunk_dims<KB>(nxt.jb0, nxt.jb1, nci, nxt.f),
-                                       sm.buf + (bi ^ 1) * C::BUF_WORDS, threadIdx.x, NTW);
+            stage_chunk<S, C::A_WORDS>(nxt.a, nxt.n, nxt.b, nxt.m, nxt.d0,
+                                       chunk_dims<KB>(nxt.jb0, nxt.jb1, nci, nxt.f), sm.buf + (bi ^ 1) * C::BUF_WORDS,
+                                       threadIdx.x, NTW);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -507,8 +518,8 @@ __global__ void PM_BOUNDS(W) plain_sk_kernel(
             fold_ctr = 0;
         }
         const uint32_t* sA = sm.buf + bi * C::BUF_WORDS;
-        compute_chunk<S>(sA, sA + C::A_WORDS, chunk_dims<KB>(cur.jb0, cur.jb1, ci, cur.f).CL, mp, acc, fold_ctr,
-                         threadIdx.x >> 5, W);
+        compute_chunk<S, C::A_WORDS>(sA, sA + C::A_WORDS, chunk_dims<KB>(cur.jb0, cur.jb1, ci, cur.f).CL, mp, acc,
+                                     fold_ctr, threadIdx.x >> 5, W);
         __syncthreads();  // this buffer is refilled by the next staging
         if (ci == cur.nchunks - 1) finish_segment<S, W>(cur, acc, mp, sm, sp, k, x0, sk, &s_last);
         if (!has_next) break;
@@ -586,6 +597,8 @@ __device__ __forceinline__ void warp_finish(const Seg& sg, uint64_t (&acc)[S], c
     // the parts, writes the outputs and resets the counter
     const int64_t ys = sg.s_tile - pbase, ye = sg.e_tile - pbase;
     const int64_t k1 = kbase + ys / Q, k2 = kbase + (ye - 1) / Q;
+    // (the scratch holds 2 slots per piece, at most wk_units_max pieces, and their counters)
+    if (!PM_CHK(k1 >= 0 && kbase + v < wk_units_max(TD) && k2 < wk_units_max(TD))) return;
     uint32_t* mine = sk.slots + (2 * (kbase + v) + (sg.x - pbase == y0 ? 0 : 1)) * TD;
 #pragma unroll
     for (int e = 0; e < S; ++e) mine[o0 + e] = r[e];
@@ -675,8 +688,8 @@ __global__ void __launch_bounds__(32 * WK_WARPS) plain_warp_kernel(
                                          c_data, c_off, 0, 0, pl.pos);
     int ci = 0, bi = 0, fold_ctr = 0;
     uint64_t acc[S];
-    stage_chunk<S, W::A_WORDS>(cur.a, cur.n, cur.b, cur.d0, chunk_dims<KB, WK_CHUNK>(cur.jb0, cur.jb1, 0, cur.f),
-                               buf, lane, 32);
+    stage_chunk<S, W::A_WORDS, WK_CHUNK>(cur.a, cur.n, cur.b, cur.m, cur.d0,
+                                         chunk_dims<KB, WK_CHUNK>(cur.jb0, cur.jb1, 0, cur.f), buf, lane, 32);
     for (;;) {
         // the chunk after this one: of this segment, of the unit's next segment, or of the next unit
         Seg nxt = cur;
@@ -700,9 +713,9 @@ __global__ void __launch_bounds__(32 * WK_WARPS) plain_warp_kernel(
             }
         }
         if (has_next) {
-            stage_chunk<S, W::A_WORDS>(nxt.a, nxt.n, nxt.b, nxt.d0,
-                                       chunk_dims<KB, WK_CHUNK>(nxt.jb0, nxt.jb1, nci, nxt.f),
-                                       buf + (bi ^ 1) * W::BUF_WORDS, lane, 32);
+            stage_chunk<S, W::A_WORDS, WK_CHUNK>(nxt.a, nxt.n, nxt.b, nxt.m, nxt.d0,
+                                                 chunk_dims<KB, WK_CHUNK>(nxt.jb0, nxt.jb1, nci, nxt.f),
+                                                 buf + (bi ^ 1) * W::BUF_WORDS, lane, 32);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -714,8 +727,9 @@ __global__ void __launch_bounds__(32 * WK_WARPS) plain_warp_kernel(
             fold_ctr = 0;
         }
         const uint32_t* sA = buf + bi * W::BUF_WORDS;
-        compute_chunk<S>(sA, sA + W::A_WORDS, chunk_dims<KB, WK_CHUNK>(cur.jb0, cur.jb1, ci, cur.f).CL, mp, acc,
-                         fold_ctr, 0, 1);
+        compute_chunk<S, W::A_WORDS, WK_CHUNK>(sA, sA + W::A_WORDS, chunk_dims<KB, WK_CHUNK>(cur.jb0, cur.jb1, ci,
+                                                                                             cur.f).CL,
+                                               mp, acc, fold_ctr, 0, 1);
         __syncwarp();  // this buffer is refilled by the next staging
         if (ci == cur.nchunks - 1) warp_finish<S>(cur, acc, mp, w.kbase, w.v, w.y0, Q, pl.pos[w.i], sk);
         if (!has_next) break;
@@ -972,87 +986,6 @@ __global__ void __launch_bounds__(256) warp_fill_kernel(int batch, WkPlan pl) {
 }
 #endif  // PM_PLAIN_STUDY_TU
 
-// The three planning steps in one CTA, for batches of at most WK_FUSED_MAX
-// pairs (one launch instead of three): the position count of every pair and
-// their total, then the scans of warp_plan_kernel (each thread keeps the pairs
-// it counted), then the unit table of warp_fill_kernel and the claim counter.
-constexpr int WK_FUSED_MAX = 32768;
-#ifndef PM_PLAIN_STUDY_TU
-__global__ void __launch_bounds__(PLAN_THREADS) warp_plan_fused_kernel(
-    int batch, const int64_t* __restrict__ a_off, const int64_t* __restrict__ b_off,
-    const int64_t* __restrict__ c_off, int64_t max_deg, int td, int64_t q_min, WkPlan pl, int* status) {
-    __shared__ long long s_scan[96];
-    __shared__ int s_bad;
-    __shared__ long long s_round[4];
-    __shared__ long long s_g;
-    const int tid = threadIdx.x;
-    const int rounds = (batch + PLAN_THREADS - 1) / PLAN_THREADS;
-    if (tid == 0) s_bad = 0;
-    {
-        long long t = 0;  // pair r PLAN_THREADS + tid is counted by thread tid (and read back by it below)
-        for (int i = tid; i < batch; i += PLAN_THREADS) {
-            int64_t n, m;
-            const int64_t np = pair_dims(i, a_off, b_off, c_off, max_deg, &n, &m) ? pair_positions(n, m, td) : -1;
-            pl.pos[i] = np;
-            if (np > 0) t += np;
-        }
-        long long d1 = 0, d2 = 0;
-        block_scan3(t, d1, d2, s_scan);
-        if (tid == PLAN_THREADS - 1) s_g = t;
-        __syncthreads();
-    }
-    const int64_t G = s_g;
-    const int64_t umax = wk_units_max(td);
-    const int64_t Q = max(q_min, (2 * G + umax - 1) / umax);
-    long long bp = 0, b0 = 0, b1 = 0, b2 = 0;
-    for (int r = 0; r < rounds; ++r) {
-        const int i = r * PLAN_THREADS + tid;
-        const int64_t np = i < batch ? pl.pos[i] : 0;
-        if (np < 0) s_bad = 1;
-        const int tier = (i >= batch || np < 0) ? 3 : (np > Q ? 0 : (8 * np >= Q ? 1 : 2));
-        const long long nu = tier == 0 ? div_up(np, Q) : 0;
-        long long xp = np > 0 ? np : 0, x0 = nu, x1 = tier == 1;
-        block_scan3(xp, x0, x1, s_scan);
-        long long x2 = tier == 2, d1 = 0, d2 = 0;
-        block_scan3(x2, d1, d2, s_scan);
-        if (i < batch) {
-            pl.pos[i] = bp + xp - (np > 0 ? np : 0);
-            pl.kbase[i] = b0 + x0 - nu;
-            pl.rank[i] = tier == 1 ? b1 + x1 - 1 : (tier == 2 ? b2 + x2 - 1 : -1);
-        }
-        if (tid == PLAN_THREADS - 1) { s_round[0] = xp; s_round[1] = x0; s_round[2] = x1; s_round[3] = x2; }
-        __syncthreads();
-        bp += s_round[0];
-        b0 += s_round[1];
-        b1 += s_round[2];
-        b2 += s_round[3];
-        __syncthreads();
-    }
-    const bool bad = s_bad != 0;
-    if (tid == 0) {
-        if (bad) atomicCAS(status, 0, (int)PM_ERR_INVALID_ARG);
-        pl.pos[batch] = G;
-        pl.kbase[batch] = b0;
-        pl.sched[0] = Q;
-        pl.sched[1] = bad ? 0 : b0;  // nothing is computed for an invalid batch
-        pl.sched[2] = bad ? 0 : b1;
-        pl.sched[3] = bad ? 0 : b2;
-        pl.sched[4] = 0;             // claim counter
-    }
-    __syncthreads();  // the prefix, bases and ranks of every pair are visible to the whole CTA
-    if (bad) return;
-    for (int i = tid; i < batch; i += PLAN_THREADS) {
-        const int64_t rk = pl.rank[i];
-        if (rk >= 0) {
-            const int64_t np = pl.pos[i + 1] - pl.pos[i];
-            pl.unit_pair[(8 * np >= Q ? b0 : b0 + b1) + rk] = i;
-        } else {
-            for (int64_t k = pl.kbase[i]; k < pl.kbase[i + 1]; ++k) pl.unit_pair[k] = i;
-        }
-    }
-}
-#endif  // PM_PLAIN_STUDY_TU
-
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
@@ -1084,7 +1017,7 @@ static cudaError_t kernel_setup(K kern, size_t smem, int dev, int* cache, int* o
 // that a call of one form never finds the other's slots where it expects
 // counters.
 constexpr int64_t COUNTER_MAX = 4096;
-constexpr int64_t COUNTER_REGION = 32768;
+constexpr int64_t COUNTER_REGION = COUNTER_REGION_DEV;
 constexpr size_t COUNTER_BYTES = COUNTER_REGION * sizeof(unsigned int);
 static_assert(wk_units_max(32) <= COUNTER_REGION && wk_units_max(256) <= COUNTER_REGION &&
                   wk_units_max(512) <= COUNTER_REGION && COUNTER_MAX <= COUNTER_REGION,
@@ -1120,6 +1053,8 @@ static pm_status launch_pair_s(const uint32_t* a, int n, const uint32_t* b, int 
     rc = ensure_scratch(&sc->sk, &sc->sk_bytes, sk_bytes(P, C::TD), st, /*zero=*/true);
     if (rc != PM_OK) return rc;
     const ModParams mp = host_mod_params(p, C::KB);
+    e = chk_bind(ws);
+    if (e != cudaSuccess) return cuda_fail(e);
     kern<<<(unsigned)P, 32 * W, C::SMEM, st>>>(a, nullptr, b, nullptr, c, nullptr, n, m, nullptr, 0, mp,
                                            sk_carve(sc->sk));
     e = cudaGetLastError();
@@ -1179,18 +1114,15 @@ static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, co
     pl.rank = pl.kbase + (batch + 1);
     pl.bsum = pl.rank + batch;
     pl.unit_pair = reinterpret_cast<int*>(pl.bsum + nblk);
+    // three planning launches: the per-pair counts and the unit table are spread over many CTAs
+    // (a one-CTA planner doing all three steps measured 12 us slower on 4096 pairs)
     const int64_t qm = q_min > 0 ? q_min : WK_MIN_UNIT;
-    int plan_launches = 1;
-    if (batch <= WK_FUSED_MAX) {
-        warp_plan_fused_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg, W::TD, qm, pl,
-                                                           ws->status);
-    } else {
-        warp_count_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>((int)batch, a_off, b_off, c_off,
-                                                                          max_deg, W::TD, pl.pos, pl.bsum);
-        warp_plan_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, W::TD, qm, pl, ws->status);
-        warp_fill_kernel<<<(unsigned)((batch + 7) / 8), 256, 0, st>>>((int)batch, pl);
-        plan_launches = 3;
-    }
+    e = chk_bind(ws);
+    if (e != cudaSuccess) return cuda_fail(e);
+    warp_count_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg,
+                                                                      W::TD, pl.pos, pl.bsum);
+    warp_plan_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, W::TD, qm, pl, ws->status);
+    warp_fill_kernel<<<(unsigned)((batch + 7) / 8), 256, 0, st>>>((int)batch, pl);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
     const ModParams mp = host_mod_params(p, Cfg<S>::KB);
@@ -1198,7 +1130,7 @@ static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, co
                                                           mp, sk);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e);
-    count_launches(1 + plan_launches);
+    count_launches(4);
     return PM_OK;
 }
 
@@ -1226,6 +1158,8 @@ static pm_status launch_batched_s(int64_t batch, const uint32_t* a_data, const i
     rc = ensure_scratch(&sc->plan, &sc->plan_bytes, sizeof(int64_t) * (size_t)(batch + 1), st, false);
     if (rc != PM_OK) return rc;
     int64_t* prefix = reinterpret_cast<int64_t*>(sc->plan);
+    e = chk_bind(ws);
+    if (e != cudaSuccess) return cuda_fail(e);
     batch_plan_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg, C::TD,
                                                   prefix, ws->status);
     e = cudaGetLastError();

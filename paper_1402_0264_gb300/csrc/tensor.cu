@@ -58,7 +58,11 @@
 namespace pm {
 
 constexpr int TT = 32;                     // outputs per block
-constexpr int NBLK = 48;                   // blocks per tile
+#ifndef PM_TC_NBLK
+#define PM_TC_NBLK 48  // output blocks per tile (a multiple of 16; 5 MMA columns each, at most 48)
+#endif
+constexpr int NBLK = PM_TC_NBLK;           // blocks per tile
+static_assert(NBLK % 16 == 0 && NBLK <= 48, "tile width");
 constexpr int NA_LIMB = 5, NB_LIMB = 4;
 constexpr int MMA_M = 128, MMA_N = NBLK * NA_LIMB;  // 240
 constexpr int TILE_OUT = TT * NBLK;        // 1536
@@ -299,6 +303,7 @@ constexpr uint32_t K_B = 0x80808080u;
 __device__ __forceinline__ void stage_a(const TcTile& tt, uint8_t* sBb, int stid, uint32_t p) {
     const int base = TT * tt.J_min;
     for (int Jr = stid; Jr < tt.nJ; Jr += STG_THREADS) {
+        if (!PM_CHK(NA_LIMB * (Jr + 1) <= ROWS_MAX)) break;  // rows (5 Jr + i) of every K chunk
         uint32_t u[TT];
 #pragma unroll
         for (int k = 0; k < TT; ++k) {
@@ -336,23 +341,20 @@ __device__ __forceinline__ void stage_b_8(const uint32_t (&u)[8], uint16_t* dst)
     }
 }
 
-// Positions [u_lo, u_hi) (groups of 8 digits) of the tile's b digits.  The Hankel
-// rows of slot gi (shifts d_lo + 8 gi .. + nds - 1) read positions
-// 1 + 32 gi .. 32 gi + 4 nds + 4, so the builders stage, before each slot, only
-// the positions it adds: the first slot of a tile waits for 37 positions, not
-// for the whole tile's 4 nd + 4.
-__device__ __forceinline__ void stage_b(const TcTile& tt, uint16_t* sbd, int btid, uint32_t p, int u_lo, int u_hi) {
-    for (int u0 = u_lo + btid; u0 < u_hi; u0 += 2 * BLD_THREADS) {
+__device__ __forceinline__ void stage_b(const TcTile& tt, uint16_t* sbd, int btid, uint32_t p) {
+    const int nu = 4 * tt.nd + 5;  // positions up to 32 nd + 39, the last one a Hankel row reads
+    if (!PM_CHK(8 * nu <= BD_LEN)) return;  // every staged position lies within a limb's array
+    for (int u0 = 1 + btid; u0 < nu; u0 += 2 * BLD_THREADS) {
         const int u1 = u0 + BLD_THREADS;
         uint32_t x0[8], x1[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
             const int g0 = tt.tb0 + 8 * u0 + v - BD_SHIFT, g1 = g0 + 8 * BLD_THREADS;
             x0[v] = (g0 >= 0 && g0 < tt.m) ? (uint32_t)centred(__ldg(tt.b + g0), p) + K_B : K_B;
-            x1[v] = (u1 < u_hi && g1 >= 0 && g1 < tt.m) ? (uint32_t)centred(__ldg(tt.b + g1), p) + K_B : K_B;
+            x1[v] = (u1 < nu && g1 >= 0 && g1 < tt.m) ? (uint32_t)centred(__ldg(tt.b + g1), p) + K_B : K_B;
         }
         stage_b_8(x0, sbd + 8 * u0);
-        if (u1 < u_hi) stage_b_8(x1, sbd + 8 * u1);
+        if (u1 < nu) stage_b_8(x1, sbd + 8 * u1);
     }
 }
 
@@ -363,6 +365,7 @@ __device__ __forceinline__ void build_hankel(const uint16_t* sbd, uint8_t* hslot
     const uint32_t* sbw = reinterpret_cast<const uint32_t*>(sbd);
     const int nrow = (4 * nds + 3) * NB_LIMB * 8;
     const int ibase = BD_SHIFT - 31 + 32 * dg - tb0;  // staged index of d_j[-31 + 32 dg]: even
+    if (!PM_CHK(nrow <= H_Q * NB_LIMB * 8 && ibase >= 0 && ibase + 8 * (4 * nds + 3) + 10 <= BD_LEN)) return;
     for (int rw = btid; rw < nrow; rw += BLD_THREADS) {
         const int t = rw & 7, j = (rw >> 3) & 3, qq = rw >> 5;
         const int e0 = j * BDS + ibase + 8 * qq + t;
@@ -480,6 +483,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                             }
 #endif
                             const uint32_t idesc = IDESC_BASE | ((nc >> 3) << 17);
+                            // a's rows of this shift and the slot's core matrices (16 row groups of
+                            // 128 bytes from the shift's K offset, two K chunks 512 bytes apart) lie
+                            // in their buffers
+                            if (!PM_CHK(NA_LIMB * (tt.d_hi - dg - s) + (int)(c0 + nc) <= ROWS_MAX &&
+                                        tt.d_hi - dg - s >= 0 && (4 * s + 7) * 512 <= H_SLOT))
+                                continue;
                             const uint32_t b_addr = sBa + (uint32_t)((NA_LIMB * (tt.d_hi - dg - s) + (int)c0) * 16);
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
@@ -573,17 +582,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             wait_parity(bar(BAR_A_FULL + sb), (k >> 1) & 1, WAIT_LIMIT);  // completed: acquires the tile record
             const TcTile tt = s_tiles[sb];
             if (tt.done) break;
+            // the whole tile's b digits at once: their loads are all in flight together, and the
+            // MMAs of the previous tile's last slots (up to NH of them) cover the time
+            stage_b(tt, sbd, btid, tp.p);
             const int ngroups = (tt.nd + GROUP_D - 1) / GROUP_D;
             bool stop = false;
-            int u_done = 1;  // b-digit positions staged so far (position 0 is never read)
             for (int gi = 0; gi < ngroups; ++gi, ++G) {
                 const int slot = (int)(G % NH);
-                // the positions this slot adds (earlier slots' rows never read them, and the
-                // previous tile's rows were all built before the sync that ended its loop)
-                const int u_need = 32 * gi + 4 * min(GROUP_D, tt.nd - gi * GROUP_D) + 5;
-                stage_b(tt, sbd, btid, tp.p, u_done, u_need);
-                u_done = u_need;
-                builders_sync();  // (the slot's b digits are complete before any row reads them)
+                builders_sync();  // (the b digits are complete before the first slot)
                 if (btid == 0) {
                     bool st = *s_abort != 0;
                     if (!st && G >= NH && !wait_parity(bar(BAR_H_EMPTY + slot), ((G / NH) - 1) & 1, WL)) {
@@ -628,7 +634,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             const uint32_t tbase = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)ab * ACC_STRIDE +
                                    (uint32_t)(half * (MMA_N / 2));
 #pragma unroll 1
-            for (int rd = 0; rd < 3; ++rd) {  // 8 blocks (40 columns) per round
+            for (int rd = 0; rd < NBLK / 16; ++rd) {  // 8 blocks (40 columns) per round
                 uint32_t v[40];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
@@ -639,7 +645,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                         : "r"(tbase + (uint32_t)(40 * rd + 8 * q)));
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (rd == 2) {  // the accumulator is free once its last columns are in registers
+                if (rd == NBLK / 16 - 1) {  // the accumulator is free once its last columns are in registers
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar(BAR_ACC_EMPTY + ab));
@@ -773,6 +779,8 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
         tp.whi[j] = (uint32_t)((w << 32) % p);
         w = (w * 256) % p;
     }
+    e = chk_bind(ws);
+    if (e != cudaSuccess) return cuda_fail(e);
     tc_plan_kernel<<<1, 1024, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg, prefix, counter, ws->status);
     tc_batched_kernel<<<ws->num_sms, TC_THREADS, TC_SMEM, st>>>((int)batch, a_data, a_off, b_data, b_off,
                                                                 c_data, c_off, prefix, counter, tp, ws->status);

@@ -13,7 +13,8 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libpolymul.so")
+# POLYMUL_LIBRARY may name another build of the same ABI (the range-checked one, _build/checked/)
+LIB_PATH = os.environ.get("POLYMUL_LIBRARY") or os.path.join(HERE, "_build", "libpolymul.so")
 
 P_DEFAULT = 469762049
 PM_AUTO, PM_PLAIN, PM_TENSOR = 0, 1, 2
