@@ -26,7 +26,10 @@
 // first inverse stage without leaving registers.  N <= 4096 runs in one CTA
 // per product.
 //
-// Arithmetic: values stay in [0, p), p < 2^30.  Multiplication by a table
+// Arithmetic: the four-step passes keep values in [0, 2p) between butterflies
+// (the lazy forms below; 4p < 2^32 since p < 2^30) and the inverse column pass's
+// final scale makes them canonical; the one-CTA path keeps them in [0, p).
+// Multiplication by a table
 // constant w uses Shoup's precomputed quotient wq = floor(w 2^32 / p)
 // (V. Shoup, NTL; also D. Harvey, "Faster arithmetic for number-theoretic
 // transforms", J. Symb. Comp. 2014): q = hi32(x wq), r = x w - q p in [0, 2p).
@@ -82,6 +85,23 @@ __device__ __forceinline__ uint32_t mul_mont(uint32_t x, uint32_t y, const NttMo
     const uint32_t q = (uint32_t)t * m.pinv_neg;
     const uint32_t u = (uint32_t)((t + (uint64_t)q * m.p) >> 32);
     return umin32(u, u - m.p);
+}
+
+// Lazy forms (D. Harvey, "Faster arithmetic for number-theoretic transforms",
+// J. Symb. Comp. 2014) for the four-step passes: values stay in [0, 2p)
+// between butterflies and only the final scale makes them canonical.
+// Shoup's product without its correction: for any x < 2^32, r in [0, 2p).
+__device__ __forceinline__ uint32_t mul_shoup_lz(uint32_t x, uint2 w, uint32_t p) {
+    return x * w.x - __umulhi(x, w.y) * p;
+}
+// v < 4p to [0, 2p) (p2 = 2p)
+__device__ __forceinline__ uint32_t r2p(uint32_t v, uint32_t p2) { return umin32(v, v - p2); }
+// Montgomery's product of x, y < 2p without its correction: (x y + q p) / 2^32 < 2p
+// since 4p < 2^32.
+__device__ __forceinline__ uint32_t mul_mont_lz(uint32_t x, uint32_t y, const NttMod& m) {
+    const uint64_t t = (uint64_t)x * y;
+    const uint32_t q = (uint32_t)t * m.pinv_neg;
+    return (uint32_t)((t + (uint64_t)q * m.p) >> 32);
 }
 
 // Frequency index k of output position `pos` of a forward transform of
@@ -194,40 +214,59 @@ __device__ void smem_ntt(uint32_t* base, int es, int ts, int cnt, bool fast_t, i
     }
 }
 
-// One radix-4 butterfly on registers with twiddle exponent e (the same
-// network as smem_ntt's; e = 0 needs no multiplications).
+// A radix-4 butterfly with the twiddles given (tw1..tw3 = w^e, w^2e, w^3e; none when
+// !on), lazy: inputs and outputs in [0, 2p).  Forward (decimation in frequency):
+// t0 = x0 + x2, t1 = x0 - x2, t2 = x1 + x3, t3 = (x1 - x3) w4, then z0 = t0 + t2,
+// z1 = (t1 + t3) w^e, z2 = (t0 - t2) w^2e, z3 = (t1 - t3) w^3e; inverse (in time): the
+// inputs x1..x3 twiddled first, the same network without output twiddles.
 template <bool FWD>
-__device__ __forceinline__ void bf4(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint2 w4,
-                                    const uint2* __restrict__ tw, int e, uint32_t p) {
-    if (!FWD && e) {
-        x1 = mul_shoup(x1, __ldg(tw + e), p);
-        x2 = mul_shoup(x2, __ldg(tw + 2 * e), p);
-        x3 = mul_shoup(x3, __ldg(tw + 3 * e), p);
+__device__ __forceinline__ void bf4t(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint2 w4, uint2 tw1,
+                                     uint2 tw2, uint2 tw3, bool on, uint32_t p) {
+    const uint32_t p2 = 2 * p;
+    if (!FWD && on) {
+        x1 = mul_shoup_lz(x1, tw1, p);
+        x2 = mul_shoup_lz(x2, tw2, p);
+        x3 = mul_shoup_lz(x3, tw3, p);
     }
-    const uint32_t t0 = add_p(x0, x2, p), t1 = sub_p(x0, x2, p);
-    const uint32_t t2 = add_p(x1, x3, p), t3 = mul_shoup(sub_p(x1, x3, p), w4, p);
-    x0 = add_p(t0, t2, p);
-    x2 = sub_p(t0, t2, p);
-    x1 = add_p(t1, t3, p);
-    x3 = sub_p(t1, t3, p);
-    if (FWD && e) {
-        x1 = mul_shoup(x1, __ldg(tw + e), p);
-        x2 = mul_shoup(x2, __ldg(tw + 2 * e), p);
-        x3 = mul_shoup(x3, __ldg(tw + 3 * e), p);
+    const uint32_t t0 = r2p(x0 + x2, p2), t1 = r2p(x0 - x2 + p2, p2);
+    const uint32_t t2 = r2p(x1 + x3, p2), t3 = mul_shoup_lz(x1 - x3 + p2, w4, p);
+    x0 = r2p(t0 + t2, p2);
+    if (FWD && on) {
+        x1 = mul_shoup_lz(t1 + t3, tw1, p);
+        x2 = mul_shoup_lz(t0 - t2 + p2, tw2, p);
+        x3 = mul_shoup_lz(t1 - t3 + p2, tw3, p);
+    } else {
+        x1 = r2p(t1 + t3, p2);
+        x2 = r2p(t0 - t2 + p2, p2);
+        x3 = r2p(t1 - t3 + p2, p2);
     }
 }
 
+// One radix-4 butterfly on registers with twiddle exponent e (the same
+// network as smem_ntt's), lazy.  The exponent varies across the lanes of a
+// warp here, so e = 0 is not special-cased: it multiplies by the table's
+// entry 0 (= 1, whose Shoup product also lands in [0, 2p)) and no lane
+// takes another path.
+template <bool FWD>
+__device__ __forceinline__ void bf4(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint2 w4,
+                                    const uint2* __restrict__ tw, int e, uint32_t p) {
+    bf4t<FWD>(x0, x1, x2, x3, w4, __ldg(tw + e), __ldg(tw + 2 * e), __ldg(tw + 3 * e), true, p);
+}
+
 // One radix-2 butterfly with twiddle exponent e (smem_ntt's radix-2 stage).
+// (lazy: inputs and outputs in [0, 2p))
 template <bool FWD>
 __device__ __forceinline__ void bf2(uint32_t& u, uint32_t& v, const uint2* __restrict__ tw, int e, uint32_t p) {
+    const uint32_t p2 = 2 * p;
+    const uint2 tv = __ldg(tw + e);  // (e = 0: entry 0 = 1, as in bf4)
     if (FWD) {
-        const uint32_t d = sub_p(u, v, p);
-        u = add_p(u, v, p);
-        v = e ? mul_shoup(d, __ldg(tw + e), p) : d;
+        const uint32_t d = u - v + p2;  // (0, 4p)
+        u = r2p(u + v, p2);
+        v = mul_shoup_lz(d, tv, p);
     } else {
-        const uint32_t w = e ? mul_shoup(v, __ldg(tw + e), p) : v;
-        v = sub_p(u, w, p);
-        u = add_p(u, w, p);
+        const uint32_t w = mul_shoup_lz(v, tv, p);
+        v = r2p(u - w + p2, p2);
+        u = r2p(u + w, p2);
     }
 }
 
@@ -333,57 +372,6 @@ __device__ void col_transform(uint32_t* sh, int logm, const uint2* __restrict__ 
 __device__ __forceinline__ int rphys(int i) { return i + (i >> 4); }
 constexpr int ROW_WORDS = NTT_N2 + NTT_N2 / 16;
 
-template <bool FWD>
-__device__ __forceinline__ void row_stage(int stage, uint32_t (&r)[16], uint2 w4, const uint2* __restrict__ tw,
-                                          uint32_t p) {
-    const int t = threadIdx.x, tp = t & 15;
-    if (FWD) {
-#pragma unroll
-        for (int l0 = 0; l0 < 4; ++l0) {
-            const int e = stage == 1 ? t + 256 * l0 : stage == 2 ? 16 * (tp + 16 * l0) : 256 * l0;
-            bf4<true>(r[l0], r[l0 + 4], r[l0 + 8], r[l0 + 12], w4, tw, e, p);
-        }
-#pragma unroll
-        for (int l1 = 0; l1 < 4; ++l1) {
-            const int e = stage == 1 ? 4 * t : stage == 2 ? 64 * tp : 0;
-            bf4<true>(r[4 * l1], r[4 * l1 + 1], r[4 * l1 + 2], r[4 * l1 + 3], w4, tw, e, p);
-        }
-    } else {
-#pragma unroll
-        for (int l1 = 0; l1 < 4; ++l1) {
-            const int e = stage == 1 ? 4 * t : stage == 2 ? 64 * tp : 0;
-            bf4<false>(r[4 * l1], r[4 * l1 + 1], r[4 * l1 + 2], r[4 * l1 + 3], w4, tw, e, p);
-        }
-#pragma unroll
-        for (int l0 = 0; l0 < 4; ++l0) {
-            const int e = stage == 1 ? t + 256 * l0 : stage == 2 ? 16 * (tp + 16 * l0) : 256 * l0;
-            bf4<false>(r[l0], r[l0 + 4], r[l0 + 8], r[l0 + 12], w4, tw, e, p);
-        }
-    }
-}
-
-// A radix-4 butterfly with the twiddles given (tw1..tw3 = w^e, w^2e, w^3e; none when !on).
-template <bool FWD>
-__device__ __forceinline__ void bf4t(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3, uint2 w4, uint2 tw1,
-                                     uint2 tw2, uint2 tw3, bool on, uint32_t p) {
-    if (!FWD && on) {
-        x1 = mul_shoup(x1, tw1, p);
-        x2 = mul_shoup(x2, tw2, p);
-        x3 = mul_shoup(x3, tw3, p);
-    }
-    const uint32_t t0 = add_p(x0, x2, p), t1 = sub_p(x0, x2, p);
-    const uint32_t t2 = add_p(x1, x3, p), t3 = mul_shoup(sub_p(x1, x3, p), w4, p);
-    x0 = add_p(t0, t2, p);
-    x2 = sub_p(t0, t2, p);
-    x1 = add_p(t1, t3, p);
-    x3 = sub_p(t1, t3, p);
-    if (FWD && on) {
-        x1 = mul_shoup(x1, tw1, p);
-        x2 = mul_shoup(x2, tw2, p);
-        x3 = mul_shoup(x3, tw3, p);
-    }
-}
-
 // row_stage on NR arrays at once (the forward transforms of a's and b's rows): every
 // twiddle is loaded once for all of them; stage 3's come from the kernel parameters.
 template <bool FWD, int NR>
@@ -398,9 +386,8 @@ __device__ __forceinline__ void row_stage_n(int stage, uint32_t (*rs[NR])[16], u
             if (stage == 3) {
                 on = l0 != 0;
                 a1 = c3[l0 ? l0 - 1 : 0][0]; a2 = c3[l0 ? l0 - 1 : 0][1]; a3 = c3[l0 ? l0 - 1 : 0][2];
-            } else {
+            } else {  // (e = 0 on some lanes: multiplied by entry 0 = 1, so no lane diverges)
                 const int e = stage == 1 ? t + 256 * l0 : 16 * (tp + 16 * l0);
-                on = e != 0;
                 a1 = __ldg(tw + e); a2 = __ldg(tw + 2 * e); a3 = __ldg(tw + 3 * e);
             }
 #pragma unroll
@@ -411,15 +398,17 @@ __device__ __forceinline__ void row_stage_n(int stage, uint32_t (*rs[NR])[16], u
         }
     };
     auto lvB = [&]() {
+        // stages 1 and 2: per-lane exponents (entry 0 = 1 where e = 0); stage 3: none for any lane
         const int e = stage == 1 ? 4 * t : stage == 2 ? 64 * tp : 0;
+        const bool on = stage != 3;
         uint2 a1 = make_uint2(0, 0), a2 = a1, a3 = a1;
-        if (e) { a1 = __ldg(tw + e); a2 = __ldg(tw + 2 * e); a3 = __ldg(tw + 3 * e); }
+        if (on) { a1 = __ldg(tw + e); a2 = __ldg(tw + 2 * e); a3 = __ldg(tw + 3 * e); }
 #pragma unroll
         for (int l1 = 0; l1 < 4; ++l1)
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
                 uint32_t (&r)[16] = *rs[k];
-                bf4t<FWD>(r[4 * l1], r[4 * l1 + 1], r[4 * l1 + 2], r[4 * l1 + 3], w4, a1, a2, a3, e != 0, p);
+                bf4t<FWD>(r[4 * l1], r[4 * l1 + 1], r[4 * l1 + 2], r[4 * l1 + 3], w4, a1, a2, a3, on, p);
             }
     };
     if (FWD) { lvA(); lvB(); } else { lvB(); lvA(); }
@@ -442,12 +431,12 @@ struct NttTables {
     uint2 st3[3][3], ist3[3][3];
 };
 
-// x * w_N^e (or w_N^-e) with e < N: w_N^e = lo[e mod 4096] * hi[e / 4096].
-__device__ __forceinline__ uint32_t mul_root(uint32_t x, uint32_t e, const uint2* lo, const uint2* hi,
-                                             uint32_t p) {
-    return mul_shoup(mul_shoup(x, __ldg(lo + (e & (NTT_N2 - 1))), p), __ldg(hi + (e >> NTT_N2_LOG)), p);
+// x * w_N^e (or w_N^-e) with e < N: w_N^e = lo[e mod 4096] * hi[e / 4096].  (The lazy
+// form: x < 2^32, result in [0, 2p).)
+__device__ __forceinline__ uint32_t mul_root_lz(uint32_t x, uint32_t e, const uint2* lo, const uint2* hi,
+                                                uint32_t p) {
+    return mul_shoup_lz(mul_shoup_lz(x, __ldg(lo + (e & (NTT_N2 - 1))), p), __ldg(hi + (e >> NTT_N2_LOG)), p);
 }
-
 // ---- N <= 4096: one CTA per product ----
 __global__ void __launch_bounds__(NTT_THREADS) ntt_small_kernel(
     const uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ b, int m,
@@ -504,7 +493,7 @@ __global__ void __launch_bounds__(NTT_THREADS, NTT_COL_MINB) ntt_col_fwd_kernel(
         const int j = idx % cols, pos = idx / cols;
         const uint32_t k1 = freq_of_pos_fast((uint32_t)pos, logn1);
         const uint32_t e = (uint32_t)(((uint64_t)(c0 + j) * k1) & nmask);
-        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root(sh[cphys(pos) * cols + j], e, tb.lo, tb.hi, md.p);
+        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root_lz(sh[cphys(pos) * cols + j], e, tb.lo, tb.hi, md.p);
     }
 }
 
@@ -555,7 +544,7 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
     }
     row_stage_n<true, 2>(3, rq, w4, tb.row, tb.st3, p);
 #pragma unroll
-    for (int l = 0; l < 16; ++l) r[l] = mul_mont(r[l], q[l], md);
+    for (int l = 0; l < 16; ++l) r[l] = mul_mont_lz(r[l], q[l], md);
     row_stage_n<false, 1>(3, ro, iw4, tb.irow, tb.ist3, p);
     __syncthreads();  // every thread has read its stage-3 inputs from sA
 #pragma unroll
@@ -577,7 +566,7 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
     for (int l = 0; l < 16; ++l) {
         const int i = t + 256 * l;
         const uint32_t e = (uint32_t)(((uint64_t)i * k1) & nmask);
-        ta[r0 + i] = mul_root(r[l], e, tb.ilo, tb.ihi, p);
+        ta[r0 + i] = mul_root_lz(r[l], e, tb.ilo, tb.ihi, p);
     }
 }
 
