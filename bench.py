@@ -793,7 +793,8 @@ def run_case(args):
                          eval_mod(a, 123456789, P) * eval_mod(b, 123456789, P) % P)  # c(r) = a(r) b(r)
         macs, name = len(a) * len(b), "degree 2^22-1 pair, transform"
     else:
-        packed = inputs.workload_batched() if args.case == "batched" else inputs.workload_tensor()
+        packed = (inputs.workload_batched(batch=args.batch or 4096) if args.case == "batched"
+                  else inputs.workload_tensor(batch=args.batch or 1024))
         max_deg = 2048 if args.case == "batched" else 4095
         mode = pm.PM_PLAIN if args.case == "batched" else pm.PM_TENSOR
         t = [torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in packed]
@@ -804,8 +805,8 @@ def run_case(args):
         check = lambda: torch.equal(out, pm.batched(t[0], t[1], t[2], t[3], t[4], max_deg=max_deg, mode=other,
                                                     total=out.numel()))
         macs = int(((packed[1][1:] - packed[1][:-1]) * (packed[3][1:] - packed[3][:-1])).sum())
-        name = ("4096 pairs, degrees log-uniform in [16,2048], plain s=%d" % s if args.case == "batched"
-                else "1024 pairs of degree 4095, tensor cores")
+        name = ("%d pairs, degrees log-uniform in [16,2048], plain s=%d" % (len(packed[1]) - 1, s)
+                if args.case == "batched" else "%d pairs of degree 4095, tensor cores" % (len(packed[1]) - 1))
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -957,6 +958,8 @@ def main():
     ap.add_argument("--s", type=int, default=0, help="fix the block parameter (skip the tuner)")
     ap.add_argument("--case", choices=["plain", "batched", "tensor", "ntt", "divide", "gcd"], default=None,
                     help="time one kernel family alone (profiling runs); prints one JSON line")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="with --case batched/tensor: the first pairs of the workload only (0 = all)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
