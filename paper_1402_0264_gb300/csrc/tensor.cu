@@ -85,14 +85,15 @@ constexpr uint32_t ACC_STRIDE = 256;
 constexpr int64_t WAIT_LIMIT = 1ll << 26;              // polls before a wait is declared lost (default)
 static_assert((BDS / 2) % 32 == 8, "limb stride must spread the limbs over the banks");
 
-// warp roles: 0 MMA issuer, 1-2 stagers (a operand), 3-10 builders (b digits,
-// Hankel slots), 11-18 epilogue
-// (8 builder warps measured fastest: 0.546 ms on 1024 pairs of degree 4095 against 0.564
-// with 4, 0.554 with 6, 0.549 with 10, 0.548 with 12)
-constexpr int STG_WARP0 = 1, STG_WARPS = 2, STG_THREADS = 32 * STG_WARPS;
+// warp roles: 0 MMA issuer, 1-4 stagers (a operand), 5-12 builders (b digits,
+// Hankel slots), 13-20 epilogue
+// (measured on 1024 pairs of degree 4095, ms: builders 4 / 6 / 8 / 10 / 12 with 2 stagers
+// 0.564 / 0.554 / 0.546 / 0.549 / 0.548; stagers 1 / 2 / 4 / 6 with 8 builders 0.597 / 0.545 /
+// 0.537 / 0.535, 4 stagers with 10 builders 0.534)
+constexpr int STG_WARP0 = 1, STG_WARPS = 4, STG_THREADS = 32 * STG_WARPS;
 constexpr int BLD_WARP0 = STG_WARP0 + STG_WARPS, BLD_WARPS = 8, BLD_THREADS = 32 * BLD_WARPS;
 constexpr int EPI_WARP0 = BLD_WARP0 + BLD_WARPS, EPI_WARPS = 8;
-constexpr int TC_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);  // 608
+constexpr int TC_THREADS = 32 * (EPI_WARP0 + EPI_WARPS);  // 672
 
 // shared memory map (bytes)
 constexpr int SM_B = 0;                                   // 2 a operands: 4 chunks x ROWS_MAX rows each
@@ -381,10 +382,10 @@ __device__ __forceinline__ void build_hankel(const uint16_t* sbd, uint8_t* hslot
 }
 
 // Warp-specialised persistent kernel.  Warp 0 issues the MMAs (one thread)
-// into two TMEM accumulators used by alternate tiles; warps 1-2 claim tiles and
+// into two TMEM accumulators used by alternate tiles; warps 1-4 claim tiles and
 // stage the a operand (double-buffered, so the next tile's is ready before the
-// current one's MMAs end); warps 3-10 stage the b digits of a tile and build its
-// Hankel slots ahead of the MMAs; warps 11-18 read an accumulator back and
+// current one's MMAs end); warps 5-12 stage the b digits of a tile and build its
+// Hankel slots ahead of the MMAs; warps 13-20 read an accumulator back and
 // reduce it while the next tile accumulates into the other one.  The roles
 // hand over through mbarriers only.
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
