@@ -230,6 +230,32 @@ def gcd_model_ratio(n: int, m: int, s: int, ell: int, U: float) -> float:
     return t1 / ts
 
 
+def fit_model_U(model_predict, points, n: int, m: int, P: float, rate: float, mhz: float) -> dict:
+    """Calibrates the model's U on measured times (the paper's U is a machine parameter
+    it leaves unvalued).  points: (s, l, ms) of one product with a n-term a and a m-term b.
+    The model's time is T_thm of Theorem 1 in units of one local operation of a block
+    (l / (rate * clock) seconds); the measured time is taken as kappa * T_thm, and U and
+    kappa minimise the squared error of log(time) over the points (U on a log grid from 1/4
+    to 64, kappa in closed form for each U).  Returns U, kappa, the rms log error and the
+    s the fitted model picks for each l."""
+    clk = mhz * 1e6
+    grid = [0.25 * 2 ** (i / 16) for i in range(16 * 8 + 1)]
+    best = None
+    for U in grid:
+        lp = [math.log(model_predict(n, m, s, ell, U, P)["T_thm"] * ell / (rate * clk)) for s, ell, _ in points]
+        lm = [math.log(ms * 1e-3) for _, _, ms in points]
+        lk = sum(b - a for a, b in zip(lp, lm)) / len(lp)
+        err = math.sqrt(sum((b - a - lk) ** 2 for a, b in zip(lp, lm)) / len(lp))
+        if best is None or err < best[0]:
+            best = (err, U, math.exp(lk))
+    err, U, kappa = best
+    picks = {}
+    for ell in sorted({e for _, e, _ in points}):
+        ss = [s for s, e, _ in points if e == ell]
+        picks[str(ell)] = min(ss, key=lambda s_: model_predict(n, m, s_, ell, U, P)["T_thm"])
+    return {"U_fit": U, "kappa": kappa, "rms_log_err": err, "best_s_fitted": picks}
+
+
 def eval_mod(poly, r: int, p: int) -> int:
     """poly(r) mod p on the host with numpy (a spot check of a product: c(r) = a(r) b(r) mod p
     for a product c = a b, the Schwartz-Zippel test).  Powers r^i as r^(i mod B) (r^B)^(i div B)."""
@@ -535,6 +561,11 @@ def measure_rows(pm, torch, dev, flush, clocks, pk, args):
         "points": {str(el): p_ for el, p_ in ell_rows.items()},
         "best_measured": {str(el): {"s": r["s"], "ms": r["ms"]} for el, r in best.items()},
         "best_thm": {str(el): min(p_, key=lambda r: r["model_T_thm_s"])["s"] for el, p_ in ell_rows.items()}}
+    # U calibrated on the 21 measured points of the study (the derived U beside it)
+    fit = fit_model_U(pm.model_predict, [(r["s"], el, r["ms"]) for el, p_ in ell_rows.items() for r in p_],
+                      N_SINGLE, N_SINGLE, float(SMS), rate, SM_MAX_MHZ)
+    fit["U_derived"] = U
+    rows["plain_ell_study"]["model_fit"] = fit
 
     # --- degree-1023 pair (latency bound) ---
     a0, b0 = inputs.workload_small()
