@@ -359,6 +359,44 @@ pm_status polymul_probe_mac_rate(int threads, int blocks_per_sm, int64_t iters, 
                                  void *stream);
 
 /*
+ * polymul_probe_mma - measures one tcgen05 MMA kind on this device, for the
+ * limb encodings of the tensor-core form (PM_TENSOR): kind PM_MMA_BF16 is
+ * kind::f16 with bf16 operands (K = 16), the one the product kernel issues;
+ * PM_MMA_E4M3 is kind::f8f6f4 with e4m3 operands (K = 32), which an
+ * encoding in 4- or 5-bit limbs would issue.  One block per SM allocates 256
+ * columns of tensor memory and, from constant operands in shared memory:
+ * (1) accumulates a sum near 2^23 with full-width MMAs and then small
+ * addends, an integer below 2^24, and checks 4 columns of all 128 lanes
+ * against it: *exact = 1 if every entry of every SM equals it (the fp32
+ * accumulation kept every bit), else 0; (2) issues `iters` full-width MMAs
+ * (M = 128, N = 256) back to back and reads the SM's cycle counter from the
+ * first issue to their completion: *flops_per_clk_sm is the mean over the
+ * SMs of 2 M N K iters over those cycles (dense flops per clock per SM, not
+ * dependent on the clock).  Synchronises `stream`; allocates (and frees) a
+ * small buffer.
+ * Returns PM_OK, PM_ERR_INVALID_ARG (null output, unknown kind, iters outside
+ * [1, 2^20]), PM_ERR_UNSUPPORTED (not an sm_100-family device, or the stream
+ * captures), PM_ERR_TIMEOUT (a bounded wait of the probe ran out), PM_ERR_NOMEM
+ * or PM_ERR_CUDA.
+ */
+/*
+ * polymul_tensor_limbs - the limb encoding of the tensor-core form
+ * (polymul_batched with PM_TENSOR): a's coefficients, moved to the centred
+ * range (-p/2, p/2], are written as *na balanced base-*base_a digits in
+ * [-base_a/2, base_a/2), b's as *nb balanced base-*base_b digits; bf16 holds
+ * every digit exactly, and an fp32 accumulator entry sums at most *max_terms
+ * digit products, so its sums stay below 2^24 and exact (products whose
+ * shorter operand is longer run in K-groups of max_terms / 32 shifts).  One
+ * modular multiply-add costs na * nb bf16 limb products.  Host only; no GPU
+ * needed.  Returns PM_OK or PM_ERR_INVALID_ARG (a null pointer).
+ */
+pm_status polymul_tensor_limbs(int *na, int *nb, uint32_t *base_a, uint32_t *base_b, int *max_terms);
+
+#define PM_MMA_BF16 0
+#define PM_MMA_E4M3 1
+pm_status polymul_probe_mma(int kind, int64_t iters, double *flops_per_clk_sm, int *exact, void *stream);
+
+/*
  * polymul_sync_status - synchronises `stream`, then returns and clears the
  * device status word of the current device (PM_OK if no kernel reported an
  * error since the last call).

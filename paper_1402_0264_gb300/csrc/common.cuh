@@ -160,6 +160,48 @@ void release_ntt_tables();
 void count_launches(uint64_t k);
 bool is_capturing(void* stream);
 
+// Programmatic dependent launch between the kernels of one call.  A kernel
+// launched by launch_dep may be scheduled while the kernel before it on the
+// stream still runs; pdl_wait, before its first access to global memory,
+// blocks until that kernel has completed and its writes are visible, so only
+// the launch, the placement of its blocks and their set-up in shared and
+// tensor memory overlap the previous kernel (no global memory access does).  pdl_trigger, at the start of the previous kernel, lets that
+// placement begin once every block of it has started.  The first kernel of a
+// call is launched the ordinary way, after everything queued before it.
+#ifndef PM_PDL
+#define PM_PDL 1
+#endif
+__device__ __forceinline__ void pdl_wait() {
+#if PM_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_trigger() {
+#if PM_PDL
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+#if PM_PDL
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+#else
+    kernel<<<grid, block, smem, st>>>(args...);
+    return cudaGetLastError();
+#endif
+}
+
 // Kernel launchers (one translation unit each).
 pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c,
                        uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws);
@@ -174,6 +216,8 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
                                 const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                 const int64_t* c_off, uint32_t p, int64_t max_deg,
                                 cudaStream_t st, DeviceWorkspace* ws);
+pm_status launch_mma_probe(int kind, int64_t iters, double* flops_per_clk_sm, int* exact, cudaStream_t st,
+                           DeviceWorkspace* ws);
 pm_status launch_plain_ell(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c, uint32_t p,
                            int s, int ell, cudaStream_t st, DeviceWorkspace* ws);
 pm_status launch_divide(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* q, uint32_t* r,

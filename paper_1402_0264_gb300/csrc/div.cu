@@ -57,6 +57,7 @@ __device__ __forceinline__ uint32_t div_mul_const(uint32_t x, uint32_t w, uint32
 __global__ void div_setup_kernel(const uint32_t* __restrict__ a, int64_t n, const uint32_t* __restrict__ b,
                                  int64_t d_b, uint32_t p, uint32_t* __restrict__ work, uint32_t* __restrict__ inv,
                                  int* status) {
+    pdl_trigger();  // the first round may be placed now; it waits for this kernel to end
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x)
         work[x] = a[x];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -96,16 +97,15 @@ __global__ void __launch_bounds__(DIV_THREADS) div_round_kernel(uint32_t* __rest
     __shared__ uint32_t sb[DIV_BODY + DIV_SMAX]; // b window of the body
     // (uniform: before any barrier) the round's steps and the body window fit the shared arrays
     if (!PM_CHK(s >= 1 && s <= DIV_SMAX && blockDim.x == DIV_THREADS)) return;
-    const uint32_t w = inv[0], wq = inv[1];
-    if (w == 0) return;  // b's leading coefficient has no inverse (status set by the setup)
     const int tid = threadIdx.x;
     const int ks = (int)min((int64_t)s, i - d_b + 1);  // division steps of this round
     const int64_t top = i - s - (int64_t)blockIdx.x * DIV_BODY;
     // b index of position x at step k is x - i + k + d_b; over this block's positions
     // (x = top - u, u < DIV_BODY) and k < s it runs over bx0 .. bx0 + DIV_BODY + s - 2
     const int64_t bx0 = top - i + d_b - (DIV_BODY - 1);
+    // b is an input no kernel of the call writes: its windows are read before the
+    // previous round has ended
     for (int t = tid; t < s; t += DIV_THREADS) {
-        head[t] = i - t >= 0 ? work[i - t] : 0u;
         const uint32_t bv = d_b - t >= 0 ? b[d_b - t] : 0u;
         bh[t] = bv;
         bhq[t] = (uint32_t)(((uint64_t)bv << 32) / p);
@@ -114,6 +114,11 @@ __global__ void __launch_bounds__(DIV_THREADS) div_round_kernel(uint32_t* __rest
         const int64_t bi = bx0 + v;
         sb[v] = (bi >= 0 && bi <= d_b) ? b[bi] : 0u;
     }
+    pdl_wait();  // the previous round's remainder (or the setup's copy and inverse)
+    pdl_trigger();
+    const uint32_t w = inv[0], wq = inv[1];
+    if (w == 0) return;  // b's leading coefficient has no inverse (status set by the setup)
+    for (int t = tid; t < s; t += DIV_THREADS) head[t] = i - t >= 0 ? work[i - t] : 0u;
     __syncthreads();
     if (tid < 32) {  // the head: one warp, the steps in order
         // Steps in groups of 32: lane j holds head entry k0 + j of the group in a
@@ -190,8 +195,8 @@ pm_status launch_divide(const uint32_t* a, int64_t n, const uint32_t* b, int64_t
     const unsigned blocks = (unsigned)std::max<int64_t>(1, (d_b + DIV_BODY - 1) / DIV_BODY);
     uint64_t launches = 1;
     for (int64_t i = n - 1; i >= d_b; i -= s, ++launches) {
-        div_round_kernel<<<blocks, DIV_THREADS, 0, st>>>(work, b, q, i, d_b, s, inv, p, mu);
-        e = cudaGetLastError();
+        e = launch_dep(div_round_kernel, dim3(blocks), dim3(DIV_THREADS), 0, st, work, b, q, i, d_b, s,
+                       (const uint32_t*)inv, p, mu);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     if (d_b > 0) {

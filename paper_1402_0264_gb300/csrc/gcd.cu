@@ -94,6 +94,7 @@ __device__ __forceinline__ uint32_t gcd_comb(uint32_t c1, uint32_t x, uint32_t c
 __global__ void gcd_init_kernel(const uint32_t* __restrict__ a, int64_t na, const uint32_t* __restrict__ b,
                                 int64_t nb, uint32_t* __restrict__ A0, uint32_t* __restrict__ B0, uint32_t p,
                                 GcdState* st) {
+    pdl_trigger();  // the first round may be placed now; it waits for this kernel to end
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < na; x += stride) A0[x] = a[x] % p;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nb; x += stride) B0[x] = b[x] % p;
@@ -144,6 +145,8 @@ __global__ void __launch_bounds__(GCD_THREADS, 1) gcd_round_kernel(
 
     // (uniform: before any barrier) the heads, step records and windows fit their arrays
     if (!PM_CHK(H <= GCD_HMAX && s <= GCD_SMAX && GCD_T + 2 * H <= GCD_WMAX && blockDim.x == GCD_THREADS)) return;
+    pdl_wait();  // the previous round's arrays and state
+    pdl_trigger();
     const GcdState s0 = *sin;
     const int tid = threadIdx.x;
     if (s0.done) {
@@ -346,6 +349,7 @@ __global__ void gcd_final_kernel(const uint32_t* __restrict__ A0, const uint32_t
                                  const uint32_t* __restrict__ A1, const uint32_t* __restrict__ B1,
                                  const GcdState* __restrict__ st, uint32_t* __restrict__ g, int64_t glen, uint32_t p,
                                  uint64_t mu, int* status) {
+    pdl_wait();  // the last round's arrays and state
     const GcdState s = *st;
     __shared__ uint32_t inv_s;
     const uint32_t* src = nullptr;
@@ -425,13 +429,9 @@ pm_status launch_gcd(const uint32_t* a, int64_t na, const uint32_t* b, int64_t n
         const unsigned blocks = (unsigned)std::max<int64_t>(1, (std::max(da, db) + GCD_T) / GCD_T);
         for (int64_t i = 0; i < batch; ++i, ++r) {
             const int x = (int)(r & 1), y = x ^ 1;
-            if (p & 1u)
-                gcd_round_kernel<true><<<blocks, GCD_THREADS, 0, st>>>(A[x], B[x], A[y], B[y], state + x, state + y,
-                                                                       s, H, y, md);
-            else
-                gcd_round_kernel<false><<<blocks, GCD_THREADS, 0, st>>>(A[x], B[x], A[y], B[y], state + x, state + y,
-                                                                        s, H, y, md);
-            e = cudaGetLastError();
+            e = launch_dep((p & 1u) ? gcd_round_kernel<true> : gcd_round_kernel<false>, dim3(blocks),
+                           dim3(GCD_THREADS), 0, st, (const uint32_t*)A[x], (const uint32_t*)B[x], A[y], B[y],
+                           (const GcdState*)(state + x), state + y, s, H, y, md);
             if (e != cudaSuccess) return cuda_fail(e);
             ++launches;
         }
@@ -443,9 +443,9 @@ pm_status launch_gcd(const uint32_t* a, int64_t na, const uint32_t* b, int64_t n
         db = host.db;
     }
     const int final_blocks = (int)std::min<int64_t>((nmax + 255) / 256, 4 * (int64_t)ws->num_sms);
-    gcd_final_kernel<<<std::max(1, final_blocks), 256, 0, st>>>(A[0], B[0], A[1], B[1], state + (r & 1), g, nmax, p,
-                                                                mu, ws->status);
-    e = cudaGetLastError();
+    e = launch_dep(gcd_final_kernel, dim3(std::max(1, final_blocks)), dim3(256), 0, st, (const uint32_t*)A[0],
+                   (const uint32_t*)B[0], (const uint32_t*)A[1], (const uint32_t*)B[1],
+                   (const GcdState*)(state + (r & 1)), g, nmax, p, mu, ws->status);
     if (e != cudaSuccess) return cuda_fail(e);
     ++launches;
     count_launches(launches);

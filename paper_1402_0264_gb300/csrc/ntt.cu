@@ -281,32 +281,42 @@ __device__ __forceinline__ void bf2(uint32_t& u, uint32_t& v, const uint2* __res
 // with one pad row after every 16 rows: element n1 of column c is
 // sh[cphys(n1) * COLS + c], cphys(n1) = n1 + n1 / 16, so that the stage whose
 // small span is 1 (16 consecutive rows per unit) reads the units of a warp
-// from distinct banks.
+// from distinct banks.  The column length 2^LOGM and every span are
+// compile-time constants, and so is each element's offset from its unit's
+// first element: for every unit of every stage, base mod 16 plus the offset
+// K mod 16 stays below 16 (all spans are powers of 4, and a unit's elements
+// below span 16 share one group of 16 rows), so cphys(base + K) =
+// cphys(base) + K + K / 16.
 __device__ __forceinline__ int cphys(int n1) { return n1 + (n1 >> 4); }
-template <bool FWD, int RS, int RL, int COLS>
-__device__ __forceinline__ void col_stage(uint32_t* sh, int logm, int lg_ss, const uint2* __restrict__ tw, uint2 w4,
-                                          uint32_t p) {
+template <bool FWD, int RS, int RL, int COLS, int LOGM, int LG_SS>
+__device__ __forceinline__ void col_stage(uint32_t* sh, const uint2* __restrict__ tw, uint2 w4, uint32_t p) {
     constexpr int R = RS * RL;
-    const int ss = 1 << lg_ss;
-    const int lg_sl = lg_ss + (RS == 4 ? 2 : 0);
-    const int nunits = COLS << (logm - (RS == 4 ? 2 : 0) - (RL == 4 ? 2 : 1));
-    for (int u = threadIdx.x; u < nunits; u += blockDim.x) {
+    constexpr int SS = 1 << LG_SS;
+    constexpr int LG_SL = LG_SS + (RS == 4 ? 2 : 0);
+    constexpr int LG_BLK = LG_SL + (RL == 4 ? 2 : 1);
+    constexpr int NUNITS = COLS << (LOGM - (RS == 4 ? 2 : 0) - (RL == 4 ? 2 : 1));
+#pragma unroll 1
+    for (int u = threadIdx.x; u < NUNITS; u += NTT_THREADS) {
         const int c = u & (COLS - 1), v = u / COLS;
-        const int j = v & (ss - 1), blk = v >> lg_ss;
-        const int base = (blk << (lg_sl + (RL == 4 ? 2 : 1))) + j;
-        if (!PM_CHK(base + ((RS - 1) << lg_ss) + ((RL - 1) << lg_sl) < (1 << logm))) continue;
+        const int j = v & (SS - 1), blk = v >> LG_SS;
+        const int base = (blk << LG_BLK) + j;
+        if (!PM_CHK(base + ((RS - 1) << LG_SS) + ((RL - 1) << LG_SL) < (1 << LOGM))) continue;
+        uint32_t* pb = sh + cphys(base) * COLS + c;
         uint32_t r[R];
 #pragma unroll
         for (int kl = 0; kl < RL; ++kl)
 #pragma unroll
-            for (int ks = 0; ks < RS; ++ks) r[ks + RS * kl] = sh[cphys(base + (ks << lg_ss) + (kl << lg_sl)) * COLS + c];
+            for (int ks = 0; ks < RS; ++ks) {
+                const int K = (ks << LG_SS) + (kl << LG_SL);
+                r[ks + RS * kl] = pb[(K + (K >> 4)) * COLS];
+            }
         // the level of span s_large: offsets j + ks s_small in its blocks
         auto large = [&]() {
 #pragma unroll
             for (int ks = 0; ks < RS; ++ks) {
-                const int jl = j + (ks << lg_ss);
-                if (RL == 4) {
-                    const int e = jl << (logm - 2 - lg_sl);
+                const int jl = j + (ks << LG_SS);
+                if constexpr (RL == 4) {
+                    const int e = jl << (LOGM - 2 - LG_SL);
                     bf4<FWD>(r[ks], r[ks + RS], r[ks + 2 * RS], r[ks + 3 * RS], w4, tw, e, p);
                 } else {
                     bf2<FWD>(r[ks], r[ks + RS], tw, jl, p);  // span M/2: twiddle exponent = offset
@@ -315,8 +325,8 @@ __device__ __forceinline__ void col_stage(uint32_t* sh, int logm, int lg_ss, con
         };
         // the level of span s_small (radix 4): offset j in its blocks
         auto small = [&]() {
-            if (RS == 4) {
-                const int e = j << (logm - 2 - lg_ss);
+            if constexpr (RS == 4) {
+                const int e = j << (LOGM - 2 - LG_SS);
 #pragma unroll
                 for (int kl = 0; kl < RL; ++kl) bf4<FWD>(r[RS * kl], r[RS * kl + 1], r[RS * kl + 2], r[RS * kl + 3], w4, tw, e, p);
             }
@@ -325,40 +335,45 @@ __device__ __forceinline__ void col_stage(uint32_t* sh, int logm, int lg_ss, con
 #pragma unroll
         for (int kl = 0; kl < RL; ++kl)
 #pragma unroll
-            for (int ks = 0; ks < RS; ++ks) sh[cphys(base + (ks << lg_ss) + (kl << lg_sl)) * COLS + c] = r[ks + RS * kl];
+            for (int ks = 0; ks < RS; ++ks) {
+                const int K = (ks << LG_SS) + (kl << LG_SL);
+                pb[(K + (K >> 4)) * COLS] = r[ks + RS * kl];
+            }
     }
     __syncthreads();
 }
 
-// The transforms of COLS side-by-side columns of length M = 2^logm (1 <= logm):
-// levels in the order of smem_ntt (forward: radix 2 at span M/2 if logm is odd,
-// then radix 4 from span M/4 or M/8 down to 1; inverse: the reverse), taken two
-// at a time.
-template <bool FWD, int COLS>
-__device__ void col_transform(uint32_t* sh, int logm, const uint2* __restrict__ tw, uint32_t p) {
-    const uint2 w4 = logm >= 2 ? __ldg(tw + (1 << (logm - 2))) : make_uint2(0, 0);
-    const int odd = logm & 1, n4 = logm >> 1;  // levels: odd radix-2, n4 radix-4
-    const int nlev = odd + n4;
-    // level i of the forward order: span log2 (logm - 1 for the radix-2 level), radix
-    auto lv_lg = [&](int i) { return odd ? (i == 0 ? logm - 1 : logm - 1 - 2 * i) : logm - 2 - 2 * i; };
-    auto lv_r2 = [&](int i) { return odd && i == 0; };
-    for (int st = 0; st < nlev; st += 2) {
-        // the forward order takes levels st, st + 1; the inverse the mirror ones
-        const int a = FWD ? st : nlev - 1 - st;   // first level executed
-        const int b = FWD ? st + 1 : nlev - 2 - st;
-        if (st + 1 < nlev) {
-            const int large = FWD ? a : b, small = FWD ? b : a;
-            if (lv_r2(large))
-                col_stage<FWD, 4, 2, COLS>(sh, logm, lv_lg(small), tw, w4, p);
-            else
-                col_stage<FWD, 4, 4, COLS>(sh, logm, lv_lg(small), tw, w4, p);
+// Levels of a length-2^LOGM column transform in the forward order: radix 2 at
+// span M/2 first when LOGM is odd, then radix 4 from span M/4 (or M/8) down to 1.
+__host__ __device__ constexpr int col_nlev(int logm) { return (logm & 1) + (logm >> 1); }
+__host__ __device__ constexpr int col_lv_lg(int logm, int i) {  // log2 of level i's span
+    return (logm & 1) ? (i == 0 ? logm - 1 : logm - 1 - 2 * i) : logm - 2 - 2 * i;
+}
+__host__ __device__ constexpr bool col_lv_r2(int logm, int i) { return (logm & 1) && i == 0; }
+
+// Stages ST, ST + 2, ... of the transform: the forward order takes levels ST and
+// ST + 1, the inverse the mirror ones.
+template <bool FWD, int COLS, int LOGM, int ST>
+__device__ __forceinline__ void col_stages(uint32_t* sh, const uint2* __restrict__ tw, uint2 w4, uint32_t p) {
+    constexpr int NLEV = col_nlev(LOGM);
+    if constexpr (ST < NLEV) {
+        constexpr int A = FWD ? ST : NLEV - 1 - ST;   // first level executed
+        if constexpr (ST + 1 < NLEV) {
+            constexpr int B = FWD ? ST + 1 : NLEV - 2 - ST;
+            constexpr int LARGE = FWD ? A : B, SMALL = FWD ? B : A;
+            col_stage<FWD, 4, col_lv_r2(LOGM, LARGE) ? 2 : 4, COLS, LOGM, col_lv_lg(LOGM, SMALL)>(sh, tw, w4, p);
         } else {
-            if (lv_r2(a))
-                col_stage<FWD, 1, 2, COLS>(sh, logm, lv_lg(a), tw, w4, p);
-            else
-                col_stage<FWD, 1, 4, COLS>(sh, logm, lv_lg(a), tw, w4, p);
+            col_stage<FWD, 1, col_lv_r2(LOGM, A) ? 2 : 4, COLS, LOGM, col_lv_lg(LOGM, A)>(sh, tw, w4, p);
         }
+        col_stages<FWD, COLS, LOGM, ST + 2>(sh, tw, w4, p);
     }
+}
+
+// The transforms of COLS side-by-side columns of length 2^LOGM (1 <= LOGM).
+template <bool FWD, int COLS, int LOGM>
+__device__ __forceinline__ void col_transform(uint32_t* sh, const uint2* __restrict__ tw, uint32_t p) {
+    const uint2 w4 = LOGM >= 2 ? __ldg(tw + (1 << (LOGM >= 2 ? LOGM - 2 : 0))) : make_uint2(0, 0);
+    col_stages<FWD, COLS, LOGM, 0>(sh, tw, w4, p);
 }
 
 // A length-4096 transform as three radix-16 stages, each two radix-4 levels
@@ -464,36 +479,38 @@ __device__ __forceinline__ void cp_async4_ntt(uint32_t* dst, const uint32_t* src
 }
 
 // ---- four-step pass 1: forward column transforms of a (y = 0) and b (y = 1) ----
-// A CTA takes `cols` adjacent columns; shared memory holds them row by row
-// ([n1][cols]), so loads and stores touch 4*cols contiguous bytes per row and
-// the butterflies of the `cols` columns run side by side.
-template <int COLS>
+// A CTA takes COLS adjacent columns of length N1 = 2^LOG1; shared memory holds
+// them row by row ([n1][COLS]), so loads and stores touch 4 COLS contiguous
+// bytes per row and the butterflies of the COLS columns run side by side.
+template <int COLS, int LOG1>
 __global__ void __launch_bounds__(NTT_THREADS, NTT_COL_MINB) ntt_col_fwd_kernel(
     const uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ b, int m,
-    uint32_t* __restrict__ ta, uint32_t* __restrict__ tb_out, int logn1, NttTables tb, NttMod md) {
-    constexpr int cols = COLS;
+    uint32_t* __restrict__ ta, uint32_t* __restrict__ tb_out, NttTables tb, NttMod md) {
+    constexpr int N1 = 1 << LOG1;
     extern __shared__ uint32_t sh[];
-    const int N1 = 1 << logn1;
-    if (!PM_CHK((blockIdx.x + 1) * cols <= NTT_N2 && blockIdx.y < 2)) return;  // (uniform: before any barrier)
+    pdl_trigger();  // the row pass may be placed now; it waits for this pass to end
+    if (!PM_CHK((blockIdx.x + 1) * COLS <= NTT_N2 && blockIdx.y < 2)) return;  // (uniform: before any barrier)
     const uint32_t* x = blockIdx.y == 0 ? a : b;
     const int len = blockIdx.y == 0 ? n : m;
     uint32_t* out = blockIdx.y == 0 ? ta : tb_out;
-    const int c0 = blockIdx.x * cols;
-    for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
-        const int j = idx % cols, n1 = idx / cols;
+    const int c0 = blockIdx.x * COLS;
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < COLS * N1; idx += NTT_THREADS) {
+        const int j = idx % COLS, n1 = idx / COLS;
         const int g = n1 * NTT_N2 + c0 + j;
-        cp_async4_ntt(sh + cphys(n1) * cols + j, x + (g < len ? g : 0), g < len);
+        cp_async4_ntt(sh + cphys(n1) * COLS + j, x + (g < len ? g : 0), g < len);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    col_transform<true, COLS>(sh, logn1, tb.hi, md.p);
-    const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
-    for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
-        const int j = idx % cols, pos = idx / cols;
-        const uint32_t k1 = freq_of_pos_fast((uint32_t)pos, logn1);
+    col_transform<true, COLS, LOG1>(sh, tb.hi, md.p);
+    constexpr uint64_t nmask = ((((uint64_t)1) << LOG1) << NTT_N2_LOG) - 1;
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < COLS * N1; idx += NTT_THREADS) {
+        const int j = idx % COLS, pos = idx / COLS;
+        const uint32_t k1 = freq_of_pos_fast((uint32_t)pos, LOG1);
         const uint32_t e = (uint32_t)(((uint64_t)(c0 + j) * k1) & nmask);
-        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root_lz(sh[cphys(pos) * cols + j], e, tb.lo, tb.hi, md.p);
+        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root_lz(sh[cphys(pos) * COLS + j], e, tb.lo, tb.hi, md.p);
     }
 }
 
@@ -505,6 +522,8 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
     __shared__ uint32_t sB[ROW_WORDS];
     const int t = threadIdx.x;
     const size_t r0 = (size_t)blockIdx.x * NTT_N2;
+    pdl_wait();  // the column pass's transforms
+    pdl_trigger();
     if (!PM_CHK(blockIdx.x < (1u << logn1) && blockDim.x == 256)) return;  // (uniform: before any barrier)
     const uint32_t p = md.p;
     const uint2 w4 = __ldg(tb.row + NTT_N2 / 4), iw4 = __ldg(tb.irow + NTT_N2 / 4);
@@ -571,29 +590,46 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
 }
 
 // ---- four-step pass 3: inverse column transforms, scale, store ----
-template <int COLS>
+template <int COLS, int LOG1>
 __global__ void __launch_bounds__(NTT_THREADS, NTT_COL_MINB) ntt_col_inv_kernel(const uint32_t* __restrict__ ta,
                                                                   uint32_t* __restrict__ c, int L,
-                                                                  int logn1, NttTables tb, NttMod md) {
-    constexpr int cols = COLS;
+                                                                  NttTables tb, NttMod md) {
+    constexpr int N1 = 1 << LOG1;
     extern __shared__ uint32_t sh[];
-    const int N1 = 1 << logn1;
-    const int c0 = blockIdx.x * cols;
-    if (!PM_CHK((blockIdx.x + 1) * cols <= NTT_N2)) return;  // (uniform: before any barrier)
-    for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
-        const int j = idx % cols, pos = idx / cols;
-        cp_async4_ntt(sh + cphys(pos) * cols + j, ta + (size_t)pos * NTT_N2 + c0 + j, true);
+    const int c0 = blockIdx.x * COLS;
+    pdl_wait();  // the row pass's products
+    if (!PM_CHK((blockIdx.x + 1) * COLS <= NTT_N2)) return;  // (uniform: before any barrier)
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < COLS * N1; idx += NTT_THREADS) {
+        const int j = idx % COLS, pos = idx / COLS;
+        cp_async4_ntt(sh + cphys(pos) * COLS + j, ta + (size_t)pos * NTT_N2 + c0 + j, true);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
-    col_transform<false, COLS>(sh, logn1, tb.ihi, md.p);
-    for (int idx = threadIdx.x; idx < cols * N1; idx += blockDim.x) {
-        const int j = idx % cols, n1 = idx / cols;
+    col_transform<false, COLS, LOG1>(sh, tb.ihi, md.p);
+#pragma unroll 4
+    for (int idx = threadIdx.x; idx < COLS * N1; idx += NTT_THREADS) {
+        const int j = idx % COLS, n1 = idx / COLS;
         const int64_t g = (int64_t)n1 * NTT_N2 + c0 + j;
-        if (g < L) c[g] = mul_shoup(sh[cphys(n1) * cols + j], tb.scale, md.p);
+        if (g < L) c[g] = mul_shoup(sh[cphys(n1) * COLS + j], tb.scale, md.p);
     }
 }
+
+// The column kernels of every log2 N1 = 1 .. 12 (blocks of 8 columns from
+// NTT_COLS8_LOG on, else 16).
+template <int LOG1>
+constexpr int col_block() { return LOG1 >= NTT_COLS8_LOG ? 8 : 16; }
+using ColFwdFn = void (*)(const uint32_t*, int, const uint32_t*, int, uint32_t*, uint32_t*, NttTables, NttMod);
+using ColInvFn = void (*)(const uint32_t*, uint32_t*, int, NttTables, NttMod);
+template <int... L>
+struct ColKernels {
+    static constexpr ColFwdFn fwd[sizeof...(L)] = {ntt_col_fwd_kernel<col_block<L>(), L>...};
+    static constexpr ColInvFn inv[sizeof...(L)] = {ntt_col_inv_kernel<col_block<L>(), L>...};
+    static constexpr int cols[sizeof...(L)] = {col_block<L>()...};
+};
+using ColTable = ColKernels<1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12>;
+static_assert(NTT_MAX_LOG - NTT_N2_LOG == 12, "column kernels for log2 N1 = 1 .. 12");
 
 // ---------------------------------------------------------------------------
 // Host side.
@@ -741,34 +777,32 @@ pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m,
     if (rc != PM_OK) return rc;
     uint32_t* ta = reinterpret_cast<uint32_t*>(sc->ntt);
     uint32_t* tbuf = ta + N;
-    const int cols = logn1 >= NTT_COLS8_LOG ? 8 : 16;  // a CTA's columns: cols * N1 words of shared memory
+    const int cols = ColTable::cols[logn1 - 1];  // a CTA's columns: cols * N1 words of shared memory
     const size_t col_rows = ((size_t)1 << logn1) + ((size_t)1 << logn1) / 16;  // with a pad row per 16
     const size_t col_smem = sizeof(uint32_t) * (size_t)cols * col_rows;
     static int col_done[64] = {};
     if (!col_done[ws->device]) {
-        // the largest block: 8 columns of N1 = 2^(NTT_MAX_LOG - 12) rows with their pad rows
-        const int n1max = 1 << (NTT_MAX_LOG - NTT_N2_LOG);
-        const int mx = (int)(sizeof(uint32_t) * 8 * (n1max + n1max / 16));
-        const void* ks[4] = {(const void*)ntt_col_fwd_kernel<8>, (const void*)ntt_col_fwd_kernel<16>,
-                             (const void*)ntt_col_inv_kernel<8>, (const void*)ntt_col_inv_kernel<16>};
-        for (const void* k : ks) {
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        for (int l = 1; l <= NTT_MAX_LOG - NTT_N2_LOG; ++l) {
+            const int rows = (1 << l) + (1 << l) / 16;
+            const int bytes = (int)(sizeof(uint32_t) * ColTable::cols[l - 1] * rows);
+            e = cudaFuncSetAttribute((const void*)ColTable::fwd[l - 1], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     bytes);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute((const void*)ColTable::inv[l - 1],
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
             if (e != cudaSuccess) return cuda_fail(e);
         }
         col_done[ws->device] = 1;
     }
-    if (cols == 8)
-        ntt_col_fwd_kernel<8><<<dim3(NTT_N2 / 8, 2), NTT_THREADS, col_smem, st>>>(a, (int)n, b, (int)m, ta, tbuf,
-                                                                                logn1, tb, md);
-    else
-        ntt_col_fwd_kernel<16><<<dim3(NTT_N2 / 16, 2), NTT_THREADS, col_smem, st>>>(a, (int)n, b, (int)m, ta,
-                                                                                  tbuf, logn1, tb, md);
-    ntt_row_kernel<<<1u << logn1, 256, 0, st>>>(ta, tbuf, logn1, tb, md);
-    if (cols == 8)
-        ntt_col_inv_kernel<8><<<NTT_N2 / 8, NTT_THREADS, col_smem, st>>>(ta, c, (int)L, logn1, tb, md);
-    else
-        ntt_col_inv_kernel<16><<<NTT_N2 / 16, NTT_THREADS, col_smem, st>>>(ta, c, (int)L, logn1, tb, md);
+    ColTable::fwd[logn1 - 1]<<<dim3(NTT_N2 / cols, 2), NTT_THREADS, col_smem, st>>>(a, (int)n, b, (int)m, ta, tbuf,
+                                                                                  tb, md);
     e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_dep(ntt_row_kernel, dim3(1u << logn1), dim3(256), 0, st, ta, (const uint32_t*)tbuf, logn1, tb,
+                       md);
+    if (e == cudaSuccess)
+        e = launch_dep(ColTable::inv[logn1 - 1], dim3(NTT_N2 / cols), dim3(NTT_THREADS), col_smem, st,
+                       (const uint32_t*)ta, c, (int)L, tb, md);
     if (e != cudaSuccess) return cuda_fail(e);
     count_launches(3);
     return PM_OK;

@@ -665,6 +665,7 @@ __global__ void __launch_bounds__(32 * WK_WARPS) plain_warp_kernel(
     extern __shared__ uint4 smem_raw[];
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     uint32_t* buf = reinterpret_cast<uint32_t*>(smem_raw) + wi * 2 * W::BUF_WORDS;
+    pdl_wait();  // the planner's schedule and unit table
     const int64_t Q = pl.sched[0];
     const int64_t tot0 = pl.sched[1];
     const int64_t U = tot0 + pl.sched[2] + pl.sched[3];
@@ -841,6 +842,7 @@ __global__ void __launch_bounds__(256) warp_count_kernel(int batch, const int64_
                                                          const int64_t* __restrict__ c_off, int64_t max_deg, int td,
                                                          int64_t* __restrict__ pos, int64_t* __restrict__ bsum) {
     __shared__ long long s_sum[8];
+    pdl_trigger();  // the planner may be placed now; it waits for this kernel to end
     const int i = blockIdx.x * 256 + threadIdx.x;
     int64_t np = 0;
     if (i < batch) {
@@ -902,6 +904,8 @@ __global__ void __launch_bounds__(PLAN_THREADS) warp_plan_kernel(int batch, int 
     __shared__ long long s_scan[96];
     __shared__ int s_bad;
     __shared__ long long s_round[4];
+    pdl_wait();  // the count kernel's per-pair counts and block sums
+    pdl_trigger();
     const int tid = threadIdx.x;
     const int rounds = (batch + PLAN_THREADS - 1) / PLAN_THREADS;
     __shared__ long long s_g;
@@ -965,6 +969,8 @@ __global__ void __launch_bounds__(PLAN_THREADS) warp_plan_kernel(int batch, int 
 // The unit table (claim order: pieces, tier 1, tier 2), one warp per pair.
 #ifndef PM_PLAIN_STUDY_TU
 __global__ void __launch_bounds__(256) warp_fill_kernel(int batch, WkPlan pl) {
+    pdl_wait();  // the plan kernel's schedule and ranks
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1121,14 +1127,16 @@ static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, co
     if (e != cudaSuccess) return cuda_fail(e);
     warp_count_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg,
                                                                       W::TD, pl.pos, pl.bsum);
-    warp_plan_kernel<<<1, PLAN_THREADS, 0, st>>>((int)batch, W::TD, qm, pl, ws->status);
-    warp_fill_kernel<<<(unsigned)((batch + 7) / 8), 256, 0, st>>>((int)batch, pl);
     e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_dep(warp_plan_kernel, dim3(1), dim3(PLAN_THREADS), 0, st, (int)batch, (int)W::TD, qm, pl,
+                       ws->status);
+    if (e == cudaSuccess)
+        e = launch_dep(warp_fill_kernel, dim3((unsigned)((batch + 7) / 8)), dim3(256), 0, st, (int)batch, pl);
     if (e != cudaSuccess) return cuda_fail(e);
     const ModParams mp = host_mod_params(p, Cfg<S>::KB);
-    kern<<<(unsigned)grid, 32 * WK_WARPS, W::SMEM, st>>>(a_data, a_off, b_data, b_off, c_data, c_off, (int)batch, pl,
-                                                          mp, sk);
-    e = cudaGetLastError();
+    e = launch_dep(kern, dim3((unsigned)grid), dim3(32 * WK_WARPS), (size_t)W::SMEM, st, a_data, a_off, b_data,
+                   b_off, c_data, c_off, (int)batch, pl, mp, sk);
     if (e != cudaSuccess) return cuda_fail(e);
     count_launches(4);
     return PM_OK;

@@ -134,3 +134,14 @@ extern "C" pm_status polymul_probe_mac_rate(int threads, int blocks_per_sm, int6
     *macs_per_clk_sm = sum / used;  // the mean over the SMs that ran blocks
     return PM_OK;
 }
+
+extern "C" pm_status polymul_probe_mma(int kind, int64_t iters, double* flops_per_clk_sm, int* exact, void* stream) {
+    if (!flops_per_clk_sm || !exact || (kind != PM_MMA_BF16 && kind != PM_MMA_E4M3) || iters < 1 ||
+        iters > (1 << 20))
+        return PM_ERR_INVALID_ARG;
+    if (is_capturing(stream)) return PM_ERR_UNSUPPORTED;
+    pm_status rc = PM_OK;
+    DeviceWorkspace* ws = workspace(stream, &rc);
+    if (!ws) return rc;
+    return launch_mma_probe(kind, iters, flops_per_clk_sm, exact, (cudaStream_t)stream, ws);
+}

@@ -52,21 +52,38 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
 
 #include "common.cuh"
 
 namespace pm {
 
 constexpr int TT = 32;                     // outputs per block
+// Limb encoding (build-time choice): 1 = 4 balanced base-160 limbs of each operand (16
+// limb products per modular MAC), 0 = 5 base-64 limbs of a x 4 base-256 limbs of b (20).
+#ifndef PM_TC_ENC
+#define PM_TC_ENC 0
+#endif
+#if PM_TC_ENC == 1
+constexpr int NA_LIMB = 4, NB_LIMB = 4;
+constexpr uint32_t BASE_A = 160, BASE_B = 160;
+constexpr int TC_MAXK = 2592;   // terms per accumulated entry: 2592 * 80 * 80 = 16588800 <= 2^24
+#else
+constexpr int NA_LIMB = 5, NB_LIMB = 4;
+constexpr uint32_t BASE_A = 64, BASE_B = 256;
+constexpr int TC_MAXK = 4096;   // 4096 * 32 * 128 = 2^24
+#endif
+static_assert((int64_t)TC_MAXK * (BASE_A / 2) * (BASE_B / 2) <= (1 << 24), "fp32 sums stay exact");
+static_assert(NB_LIMB == 4, "M = 128 rows: 4 limbs of b x 32 offsets");
 #ifndef PM_TC_NBLK
-#define PM_TC_NBLK 48  // output blocks per tile (a multiple of 16; 5 MMA columns each, at most 48)
+#define PM_TC_NBLK 48  // output blocks per tile (a multiple of 16)
 #endif
 constexpr int NBLK = PM_TC_NBLK;           // blocks per tile
-static_assert(NBLK % 16 == 0 && NBLK <= 48, "tile width");
-constexpr int NA_LIMB = 5, NB_LIMB = 4;
-constexpr int MMA_M = 128, MMA_N = NBLK * NA_LIMB;  // 240
+constexpr int MMA_M = 128, MMA_N = NBLK * NA_LIMB;  // 192 (4 limbs of a) or 240 (5)
+static_assert(NBLK % 16 == 0 && MMA_N <= 256, "tile width");
 constexpr int TILE_OUT = TT * NBLK;        // 1536
-constexpr int TC_MAXK = 4096;              // exactness bound: terms per accumulated entry
 constexpr int TC_GROUP = TC_MAXK / TT;     // shifts per K-group when both operands are longer
 constexpr int64_t TC_MAX_DEG = PM_TENSOR_MAX_DEG;      // degrees this path takes (int tile indices)
 constexpr int GROUP_D = 8;                 // shifts per Hankel slot
@@ -74,7 +91,9 @@ constexpr int NH = 4;                      // Hankel slots in the ring
 constexpr int MAX_DELTA = TC_MAXK / TT + 2;            // shifts a tile can need
 constexpr int BD_SHIFT = 7;                            // staged b digit t sits at index t + 7
 constexpr int BD_LEN = TT * (MAX_DELTA + 2);           // b digits staged per limb (with the shift)
-constexpr int BDS = BD_LEN + 16;                       // limb stride: 4 limbs on 4 distinct bank groups
+// limb stride in bf16 elements: an odd multiple of 8 words apart mod 32, so the 4 limbs sit on
+// distinct bank groups
+constexpr int BDS = BD_LEN + 2 * ((8 - (BD_LEN / 2) % 32 + 32) % 32);
 constexpr int ROWS_MAX = NA_LIMB * (NBLK + MAX_DELTA + 2);
 constexpr int B_LBO = ROWS_MAX * 16;                   // bytes between K chunks of the a operand
 constexpr int B_BUF = 4 * B_LBO;                       // one a operand (double-buffered across tiles)
@@ -129,13 +148,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
     return d;
 }
 
-// instruction descriptor: D f32, A and B bf16, both K-major, M = 128; the N field
-// (bits 17-22, N / 8) is or-ed in per MMA (N a multiple of 16, at most 240)
+// instruction descriptor: D f32, A and B bf16, both K-major, N / 8 in bits 17-22, M / 16
+// in bits 24-28 (every MMA spans the tile's full width: MMAs narrowed to the blocks a
+// shift meets measured slower at every granularity)
 constexpr uint32_t IDESC_BASE = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(MMA_M >> 4) << 24);
-
-#ifndef PM_TC_NARROW
-#define PM_TC_NARROW 0  // 1: MMAs cover only the columns a shift meets (build-time choice)
-#endif
+constexpr uint32_t IDESC = IDESC_BASE | ((uint32_t)(MMA_N >> 3) << 17);
+static_assert(MMA_N % 16 == 0 && MMA_N <= 256, "MMA width");
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
     asm volatile(
@@ -287,26 +305,50 @@ struct TcParams {
     uint32_t p;
     uint64_t mu;             // floor(2^64 / p)
     uint64_t off;            // a multiple of p above 2^52 (makes signed limb sums non-negative)
-    uint32_t wlo[NB_LIMB];   // 256^j mod p
-    uint32_t whi[NB_LIMB];   // 2^32 * 256^j mod p
+    uint32_t wlo[NB_LIMB];   // BASE_B^j mod p
+    uint32_t whi[NB_LIMB];   // 2^32 * BASE_B^j mod p
     int64_t wait_limit;      // polls before a wait between the roles is declared lost
 };
 
-// Balanced digits by an offset: with K = 32 (1 + 64 + ... + 64^4), u = v + K
-// lies in [0, 2^30) for |v| < p/2 < 2^28, its standard base-64 digits f_i give
-// v = sum (f_i - 32) 64^i, the balanced digits in [-32, 31].  Likewise base 256
-// with K = 128 (1 + 256 + 256^2 + 256^3) = 0x80808080 for the 4 digits of b.
-constexpr uint32_t K_A = 32u * (1u + 64u + 4096u + 262144u + 16777216u);
-constexpr uint32_t K_B = 0x80808080u;
+// Balanced digits by an offset: with K = (B / 2) (1 + B + ... + B^(L-1)), u = v + K
+// lies in [0, B^L) for |v| < p/2 < 2^28 (B = 160, L = 4: K = 329740880 and u in
+// [61305424, 598176336]; B = 64, L = 5 and B = 256, L = 4 likewise), its standard
+// base-B digits f_i give v = sum (f_i - B/2) B^i, the balanced digits in [-B/2, B/2).
+template <uint32_t B, int L>
+__host__ __device__ constexpr uint32_t digit_offset() {
+    uint32_t k = 0, w = 1;
+    for (int i = 0; i < L; ++i) {
+        k += (B / 2) * w;
+        w *= B;
+    }
+    return k;
+}
+constexpr uint32_t K_A = digit_offset<BASE_A, NA_LIMB>();
+constexpr uint32_t K_B = digit_offset<BASE_B, NB_LIMB>();
+template <uint32_t B, int L>
+__host__ __device__ constexpr uint64_t digit_span() {  // B^L
+    uint64_t w = 1;
+    for (int i = 0; i < L; ++i) w *= B;
+    return w;
+}
+static_assert(K_A >= (1u << 28) && (uint64_t)K_A + (1u << 28) <= digit_span<BASE_A, NA_LIMB>(), "digits of a");
+static_assert(K_B >= (1u << 28) && (uint64_t)K_B + (1u << 28) <= digit_span<BASE_B, NB_LIMB>(), "digits of b");
 
-// a operand of a tile: row (5 Jr + i) of K chunk kc holds limb i of
+// the next digit of u (u % B as bf16 bits of the balanced digit) and u / B
+template <uint32_t B>
+__device__ __forceinline__ uint32_t next_digit(uint32_t& u) {
+    const uint32_t q = u / B, f = u - q * B;
+    u = q;
+    return digit_bits<B / 2>(f);
+}
+
+// a operand of a tile: row (NA_LIMB Jr + i) of K chunk kc holds limb i of
 // a[32 (J_min + Jr) + 31 - 8 kc - e] at element e (K runs backwards).  One
-// thread per block Jr: 32 coefficients, 5 limbs x 4 chunks of 16 bytes;
-// neighbouring threads write rows 80 bytes apart (distinct bank groups).
+// thread per block Jr: 32 coefficients, NA_LIMB limbs x 4 chunks of 16 bytes.
 __device__ __forceinline__ void stage_a(const TcTile& tt, uint8_t* sBb, int stid, uint32_t p) {
     const int base = TT * tt.J_min;
     for (int Jr = stid; Jr < tt.nJ; Jr += STG_THREADS) {
-        if (!PM_CHK(NA_LIMB * (Jr + 1) <= ROWS_MAX)) break;  // rows (5 Jr + i) of every K chunk
+        if (!PM_CHK(NA_LIMB * (Jr + 1) <= ROWS_MAX)) break;  // rows (NA_LIMB Jr + i) of every K chunk
         uint32_t u[TT];
 #pragma unroll
         for (int k = 0; k < TT; ++k) {
@@ -318,7 +360,7 @@ __device__ __forceinline__ void stage_a(const TcTile& tt, uint8_t* sBb, int stid
         for (int i = 0; i < NA_LIMB; ++i) {
             uint32_t f[TT];
 #pragma unroll
-            for (int k = 0; k < TT; ++k) f[k] = digit_bits<32>((u[k] >> (6 * i)) & 63u);
+            for (int k = 0; k < TT; ++k) f[k] = next_digit<BASE_A>(u[k]);
 #pragma unroll
             for (int kc = 0; kc < 4; ++kc) {  // elements e = 0..7 are k = 31 - 8 kc - e
                 const int k0 = 31 - 8 * kc;
@@ -333,12 +375,12 @@ __device__ __forceinline__ void stage_a(const TcTile& tt, uint8_t* sBb, int stid
 // b digits in natural order: position x of limb j holds d_j[tb0 + x - BD_SHIFT].
 // One thread per 8 positions (positions 0..7 are never read), two groups of 8
 // per pass so that their loads are in flight together.
-__device__ __forceinline__ void stage_b_8(const uint32_t (&u)[8], uint16_t* dst) {
+__device__ __forceinline__ void stage_b_8(uint32_t (&u)[8], uint16_t* dst) {
 #pragma unroll
     for (int j = 0; j < NB_LIMB; ++j) {
         uint32_t f[8];
 #pragma unroll
-        for (int v = 0; v < 8; ++v) f[v] = digit_bits<128>(__byte_perm(u[v], 0, 0x4440 + j));
+        for (int v = 0; v < 8; ++v) f[v] = next_digit<BASE_B>(u[v]);
         *reinterpret_cast<uint4*>(dst + j * BDS) =
             make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
     }
@@ -433,6 +475,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *s_tmem;
+    pdl_wait();  // the planner's prefix and counter (nothing above touches global memory)
     const int64_t total = prefix[batch];
     const int64_t WL = tp.wait_limit;
 
@@ -470,34 +513,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
                         const int dg = tt.d_lo + gi * GROUP_D;
                         for (int s = 0; s < nds; ++s) {
                             const bool first = gi == 0 && s == 0;
-                            uint32_t c0 = 0, nc = MMA_N;  // columns of this shift's MMAs
-#if PM_TC_NARROW
-                            // Shift d meets the tile's blocks lo .. hi (those whose block of a,
-                            // I - d, exists and which hold outputs); its MMAs cover their
-                            // columns, widened to multiples of 16.  The first shift spans all
-                            // 240 columns, since it initialises the accumulator.
-                            if (!first) {
-                                const int d = dg + s;
-                                const int lo = max(0, d - tt.I0);
-                                const int hi = min(min(NBLK - 1, d + tt.na - 1 - tt.I0), (tt.L - 1) / TT - tt.I0);
-                                if (hi < lo) continue;  // no output of the tile gets a term from this shift
-                                c0 = (uint32_t)(NA_LIMB * lo) & ~15u;
-                                nc = min((uint32_t)MMA_N, (uint32_t)(NA_LIMB * hi + NA_LIMB + 15) & ~15u) - c0;
-                            }
-#endif
-                            const uint32_t idesc = IDESC_BASE | ((nc >> 3) << 17);
                             // a's rows of this shift and the slot's core matrices (16 row groups of
                             // 128 bytes from the shift's K offset, two K chunks 512 bytes apart) lie
                             // in their buffers
-                            if (!PM_CHK(NA_LIMB * (tt.d_hi - dg - s) + (int)(c0 + nc) <= ROWS_MAX &&
+                            if (!PM_CHK(NA_LIMB * (tt.d_hi - dg - s) + MMA_N <= ROWS_MAX &&
                                         tt.d_hi - dg - s >= 0 && (4 * s + 7) * 512 <= H_SLOT))
                                 continue;
-                            const uint32_t b_addr = sBa + (uint32_t)((NA_LIMB * (tt.d_hi - dg - s) + (int)c0) * 16);
+                            const uint32_t b_addr = sBa + (uint32_t)(NA_LIMB * (tt.d_hi - dg - s) * 16);
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 const uint64_t da = smem_desc(ha + (uint32_t)((4 * s + 2 * h) * 512), 512, 128);
                                 const uint64_t db = smem_desc(b_addr + 2 * h * B_LBO, B_LBO, 128);
-                                mma_bf16(tacc + c0, da, db, idesc, (first && h == 0) ? 0u : 1u);
+                                mma_bf16(tacc, da, db, IDESC, (first && h == 0) ? 0u : 1u);
                             }
                         }
                         mma_commit(bar(BAR_H_EMPTY + slot));
@@ -637,15 +664,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
             const uint32_t tbase = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)ab * ACC_STRIDE +
                                    (uint32_t)(half * (MMA_N / 2));
 #pragma unroll 1
-            for (int rd = 0; rd < NBLK / 16; ++rd) {  // 8 blocks (40 columns) per round
-                uint32_t v[40];
+            for (int rd = 0; rd < NBLK / 16; ++rd) {  // 8 blocks (8 NA_LIMB columns) per round
+                uint32_t v[8 * NA_LIMB];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
+                for (int q = 0; q < NA_LIMB; ++q) {
                     asm volatile(
                         "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                         : "=r"(v[8 * q + 0]), "=r"(v[8 * q + 1]), "=r"(v[8 * q + 2]), "=r"(v[8 * q + 3]),
                           "=r"(v[8 * q + 4]), "=r"(v[8 * q + 5]), "=r"(v[8 * q + 6]), "=r"(v[8 * q + 7])
-                        : "r"(tbase + (uint32_t)(40 * rd + 8 * q)));
+                        : "r"(tbase + (uint32_t)(8 * NA_LIMB * rd + 8 * q)));
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (rd == NBLK / 16 - 1) {  // the accumulator is free once its last columns are in registers
@@ -659,16 +686,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
 #pragma unroll
                     for (int be = 0; be < 4; ++be) {
                         const uint32_t* dv = v + NA_LIMB * (4 * c4 + be);
-                        const int d0 = __float2int_rn(__uint_as_float(dv[0]));
-                        const int d1 = __float2int_rn(__uint_as_float(dv[1]));
-                        const int d2 = __float2int_rn(__uint_as_float(dv[2]));
-                        const int d3 = __float2int_rn(__uint_as_float(dv[3]));
-                        const int d4 = __float2int_rn(__uint_as_float(dv[4]));
-                        // sum_i 64^i d_i: d0 + 64 d1 and d2 + 64 d3 fit in 31 bits (|d_i| <= 2^24)
-                        int64_t sum = (int64_t)(d2 + 64 * d3) * 4096 + (int64_t)tp.off;
-                        sum += (int64_t)d4 * (1 << 24);
-                        sum += (int64_t)(d0 + 64 * d1);
-                        const uint64_t u = (uint64_t)sum;  // in [0, 2^53)
+                        // off + sum_i BASE_A^i d_i with |d_i| <= 2^24: |sum| < 2^49, so u lies in [0, 2^53)
+                        int64_t sum = (int64_t)tp.off;
+                        int64_t wa = 1;
+#pragma unroll
+                        for (int i = 0; i < NA_LIMB; ++i) {
+                            sum += (int64_t)__float2int_rn(__uint_as_float(dv[i])) * wa;
+                            wa *= BASE_A;
+                        }
+                        const uint64_t u = (uint64_t)sum;
                         x[be] = (uint64_t)(uint32_t)u * wlo + (uint64_t)(uint32_t)(u >> 32) * whi;  // < 2^61.01
                     }
                     // reduce-scatter over the limbs: lane (j, t) ends with block 4 c4 + j
@@ -707,6 +733,7 @@ __global__ void __launch_bounds__(1024) tc_plan_kernel(int batch, const int64_t*
                                                         int64_t* prefix, unsigned long long* counter, int* status) {
     __shared__ long long s_scan[1024];
     __shared__ int s_bad;
+    pdl_trigger();  // the product kernel may be placed now; it waits for this one to end
     const int tid = threadIdx.x;
     if (tid == 0) s_bad = 0;
     __syncthreads();
@@ -750,6 +777,194 @@ __global__ void __launch_bounds__(1024) tc_plan_kernel(int batch, const int64_t*
     }
 }
 
+// ---- Measurement: the rate and the exactness of one tcgen05 MMA kind ----
+// kind 0: kind::f16 with bf16 operands (K = 16 per MMA, the product kernel's
+// kind); kind 1: kind::f8f6f4 with e4m3 operands (K = 32), the 8-bit limb
+// encoding's.  Every operand is a constant, so the result does not depend on
+// the core-matrix layout: A holds `big` (bf16 128 or e4m3 16) or 1, B holds 1.
+// Exactness: r_big MMAs of the big A and then r_small of A = 1 accumulate
+// r_big K big + r_small K, an integer below 2^24 that fp32 holds exactly, into
+// every accumulator entry; the small addends land on a sum near 2^23, so an
+// accumulation that kept fewer bits than fp32 would drop them.  Rate: r_rate
+// further full-width MMAs (M = 128, N = 256) issued back to back by one
+// thread, timed on the SM's cycle counter from the first issue to their
+// completion (commit and wait).  Each wait is bounded.
+constexpr int MP_THREADS = 128, MP_N = 256;
+constexpr int MP_A_BYTES = 128 * 32, MP_B_BYTES = MP_N * 32;  // rows x 32 bytes of K
+constexpr int MP_SMEM = 2 * MP_A_BYTES + MP_B_BYTES + 64;
+
+struct MmaProbeRec {
+    long long start, end;
+    uint32_t value, mismatches;
+    int smid, status;
+};
+
+__device__ __forceinline__ void mma_probe_issue(int kind, uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                                uint32_t acc) {
+    if (kind == 0) {
+        mma_bf16(tmem, da, db, idesc, acc);
+    } else {
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+    }
+}
+
+__global__ void __launch_bounds__(MP_THREADS, 1) tc_mma_probe_kernel(int kind, int r_big, int r_small, int r_rate,
+                                                                      uint32_t expect_bits,
+                                                                      MmaProbeRec* __restrict__ rec) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    uint8_t* a_big = sm;
+    uint8_t* a_one = sm + MP_A_BYTES;
+    uint8_t* b_one = sm + 2 * MP_A_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + 2 * MP_A_BYTES + MP_B_BYTES);  // [0] phases, [1] drain
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2);
+    int* s_status = reinterpret_cast<int*>(bars + 3);
+    uint32_t* s_bad = reinterpret_cast<uint32_t*>(bars + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t w_big = kind ? 0x58585858u : 0x43004300u;  // e4m3 16.0 / bf16 128.0
+    const uint32_t w_one = kind ? 0x38383838u : 0x3F803F80u;  // e4m3 1.0 / bf16 1.0
+    for (int i = tid; i < MP_A_BYTES / 4; i += MP_THREADS) {
+        reinterpret_cast<uint32_t*>(a_big)[i] = w_big;
+        reinterpret_cast<uint32_t*>(a_one)[i] = w_one;
+    }
+    for (int i = tid; i < MP_B_BYTES / 4; i += MP_THREADS) reinterpret_cast<uint32_t*>(b_one)[i] = w_one;
+    if (tid == 0) {
+        mbar_init(smem_u32(&bars[0]), 1);
+        mbar_init(smem_u32(&bars[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *s_status = 0;
+        *s_bad = 0;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // operands visible to the tensor core
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(MP_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *s_tmem;
+    const uint32_t idesc = (1u << 4) | (kind ? 0u : ((1u << 7) | (1u << 10))) | ((uint32_t)(MP_N >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    const uint64_t da_big = smem_desc(smem_u32(a_big), 128, 256);
+    const uint64_t da_one = smem_desc(smem_u32(a_one), 128, 256);
+    const uint64_t db = smem_desc(smem_u32(b_one), 128, 256);
+    if (tid == 0) {
+        for (int i = 0; i < r_big; ++i) mma_probe_issue(kind, tmem, da_big, db, idesc, i > 0 ? 1u : 0u);
+        for (int i = 0; i < r_small; ++i) mma_probe_issue(kind, tmem, da_one, db, idesc, 1u);
+        mma_commit(smem_u32(&bars[0]));
+        if (!wait_parity(smem_u32(&bars[0]), 0, WAIT_LIMIT)) *s_status = PM_ERR_TIMEOUT;
+    }
+    __syncthreads();
+    if (*s_status == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // each warp reads its 32 lanes at 4 columns spread over the accumulator
+        uint32_t v[4];
+        const uint32_t base = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                         : "=r"(v[q])
+                         : "r"(base + (uint32_t)(q * (MP_N / 4) + 17 * q)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        uint32_t bad = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bad += v[q] != expect_bits;
+        if (bad) atomicAdd(s_bad, bad);
+        if (tid == 0) rec[blockIdx.x].value = v[0];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        long long t0 = clock64(), t1 = t0;
+        if (*s_status == 0) {
+            for (int i = 0; i < r_rate; ++i) mma_probe_issue(kind, tmem, da_big, db, idesc, i > 0 ? 1u : 0u);
+            mma_commit(smem_u32(&bars[0]));
+            if (!wait_parity(smem_u32(&bars[0]), 1, WAIT_LIMIT)) *s_status = PM_ERR_TIMEOUT;
+            t1 = clock64();
+        }
+        // every MMA this thread issued is complete before the tensor memory is freed
+        mma_commit(smem_u32(&bars[1]));
+        if (!wait_parity(smem_u32(&bars[1]), 0, WAIT_LIMIT)) *s_status = PM_ERR_TIMEOUT;
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        rec[blockIdx.x].start = t0;
+        rec[blockIdx.x].end = t1;
+        rec[blockIdx.x].smid = (int)smid;
+        rec[blockIdx.x].status = *s_status;
+        rec[blockIdx.x].mismatches = *s_bad;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MP_N));
+    }
+}
+
+pm_status launch_mma_probe(int kind, int64_t iters, double* flops_per_clk_sm, int* exact, cudaStream_t st,
+                           DeviceWorkspace* ws) {
+    if (ws->cc_major != 10) return PM_ERR_UNSUPPORTED;  // tcgen05 needs the sm_100 family
+    const int nblk = ws->num_sms;
+    const int K = kind ? 32 : 16, big = kind ? 16 : 128;
+    // r_big MMAs bring the sum near 2^23; r_small addends follow (exact integers below 2^24)
+    const int r_big = (int)(((1 << 23) - 1) / ((int64_t)K * big)), r_small = 300;
+    const float expect = (float)((int64_t)r_big * K * big + (int64_t)r_small * K);
+    uint32_t expect_bits;
+    memcpy(&expect_bits, &expect, sizeof(expect_bits));
+    MmaProbeRec* d_rec = nullptr;
+    if (dev_alloc((void**)&d_rec, sizeof(MmaProbeRec) * (size_t)nblk) != cudaSuccess) {
+        cudaGetLastError();
+        return PM_ERR_NOMEM;
+    }
+    std::vector<MmaProbeRec> h((size_t)nblk);
+    cudaError_t e = cudaFuncSetAttribute(tc_mma_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MP_SMEM);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_rec, 0, sizeof(MmaProbeRec) * (size_t)nblk, st);
+    if (e == cudaSuccess) {
+        tc_mma_probe_kernel<<<nblk, MP_THREADS, MP_SMEM, st>>>(kind, r_big, r_small, (int)iters, expect_bits, d_rec);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d_rec, sizeof(MmaProbeRec) * (size_t)nblk, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_rec);
+    if (e != cudaSuccess) return cuda_fail(e);
+    count_launches(1);
+    // per SM: the MMAs of its blocks over the cycles from its first start to its last end
+    std::map<int, std::pair<long long, long long>> span;
+    std::map<int, int> cnt;
+    int ok = 1;
+    for (const MmaProbeRec& r : h) {
+        if (r.status != 0) return (pm_status)r.status;
+        if (r.mismatches != 0 || r.value != expect_bits) ok = 0;
+        auto it = span.find(r.smid);
+        if (it == span.end()) {
+            span[r.smid] = {r.start, r.end};
+        } else {
+            it->second.first = std::min(it->second.first, r.start);
+            it->second.second = std::max(it->second.second, r.end);
+        }
+        ++cnt[r.smid];
+    }
+    const double flops = 2.0 * 128 * MP_N * K * (double)iters;
+    double sum = 0.0;
+    int used = 0;
+    for (const auto& kv : span) {
+        const long long c = kv.second.second - kv.second.first;
+        if (c <= 0) continue;
+        sum += flops * cnt[kv.first] / (double)c;
+        ++used;
+    }
+    if (!used) return PM_ERR_INTERNAL;
+    *flops_per_clk_sm = sum / used;
+    *exact = ok;
+    return PM_OK;
+}
+
 pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                 const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                 const int64_t* c_off, uint32_t p, int64_t max_deg, cudaStream_t st,
@@ -780,17 +995,28 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
     for (int j = 0; j < NB_LIMB; ++j) {
         tp.wlo[j] = (uint32_t)w;
         tp.whi[j] = (uint32_t)((w << 32) % p);
-        w = (w * 256) % p;
+        w = (w * BASE_B) % p;
     }
     e = chk_bind(ws);
     if (e != cudaSuccess) return cuda_fail(e);
     tc_plan_kernel<<<1, 1024, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg, prefix, counter, ws->status);
-    tc_batched_kernel<<<ws->num_sms, TC_THREADS, TC_SMEM, st>>>((int)batch, a_data, a_off, b_data, b_off,
-                                                                c_data, c_off, prefix, counter, tp, ws->status);
     e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = launch_dep(tc_batched_kernel, dim3(ws->num_sms), dim3(TC_THREADS), TC_SMEM, st, (int)batch, a_data,
+                       a_off, b_data, b_off, c_data, c_off, (const int64_t*)prefix, counter, tp, ws->status);
     if (e != cudaSuccess) return cuda_fail(e);
     count_launches(2);
     return PM_OK;
 }
 
 }  // namespace pm
+
+extern "C" pm_status polymul_tensor_limbs(int* na, int* nb, uint32_t* base_a, uint32_t* base_b, int* max_terms) {
+    if (!na || !nb || !base_a || !base_b || !max_terms) return PM_ERR_INVALID_ARG;
+    *na = pm::NA_LIMB;
+    *nb = pm::NB_LIMB;
+    *base_a = pm::BASE_A;
+    *base_b = pm::BASE_B;
+    *max_terms = pm::TC_MAXK;
+    return PM_OK;
+}

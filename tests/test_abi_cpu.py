@@ -44,6 +44,19 @@ def test_debug_knob_validation(lib):
     assert lib.polymul_debug_set(pm.PM_DEBUG_FAIL_ALLOC, 0) == 0
 
 
+def test_probe_validation_happens_on_host(lib):
+    r = ctypes.c_double(0.0)
+    ex = ctypes.c_int(0)
+    f = lib.polymul_probe_mma
+    assert f(7, 16, ctypes.byref(r), ctypes.byref(ex), NULL) == 1           # unknown kind
+    assert f(pm.PM_MMA_BF16, 0, ctypes.byref(r), ctypes.byref(ex), NULL) == 1  # no MMAs
+    assert f(pm.PM_MMA_E4M3, 1 << 21, ctypes.byref(r), ctypes.byref(ex), NULL) == 1
+    assert f(pm.PM_MMA_E4M3, 16, None, ctypes.byref(ex), NULL) == 1
+    g = lib.polymul_probe_mac_rate
+    assert g(33, 1, 100, ctypes.byref(r), NULL) == 1                         # not a multiple of 32
+    assert g(256, 0, 100, ctypes.byref(r), NULL) == 1
+
+
 def test_status_strings(lib):
     for code in range(8):
         assert lib.polymul_status_string(code)
