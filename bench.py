@@ -13,7 +13,7 @@ Headline step: the batched tensor-core product of 1024 pairs of degree 4095
 with PM_TENSOR (a planning launch and one persistent tcgen05 kernel).  Each
 timed step is bracketed by CUDA events on the launching stream and preceded
 by a 256 MiB write that flushes the 129 MB L2 (outside the events).  The
-roofline is the tensor one: 20 bf16 limb products per modular MAC (2 flops
+roofline is the tensor one: the bf16 limb products of the encoding per modular MAC (2 flops
 each) over the measured bf16 peak.  The one-pair degree-16383 product of
 the s-blocked plain kernel (the paper's Section 5 form) is the row
 `plain_single`, with its own ALU roofline, e2e and CPU baseline.
@@ -49,8 +49,6 @@ METRIC = "modular coefficient MACs/s (n*m per product), bit-exact vs oracle"
 UNIT = "MAC/s"
 BATCH_T, DEG_T = 1024, 4095
 MACS_T = BATCH_T * (DEG_T + 1) ** 2        # 1.718e10 modular multiply-adds per step
-LIMB_PRODUCTS = 20                          # 5 balanced base-64 limbs of a x 4 base-256 limbs of b
-FLOPS_PER_MAC = 2 * LIMB_PRODUCTS           # bf16 flops of useful tensor work per modular MAC
 WORKLOAD = ("batched tensor-core polymul mod p=469762049: 1024 pairs of degree 4095, uint32 coefficients "
             "uniform in [0,p), bf16 limbs on tcgen05 with exact fp32 accumulation and a fused mod-p epilogue")
 N_SINGLE = 16384
@@ -325,13 +323,11 @@ def run_reference(args, world, rank):
 # our arm
 # ---------------------------------------------------------------------------
 
-TC_CHUNK_BLOCKS = 48  # output blocks of 32 per MMA column chunk of the tensor kernel (5 columns each)
-
-
-def tc_issued_flops(a_off, b_off) -> float:
-    """bf16 flops the tensor kernel issues for a batch (padding included): per tile of 1536
-    outputs (48 blocks) and per shift it meets, 2 MMAs of 128 x N x 16, N = 5 columns per block
-    over the chunks of TC_CHUNK_BLOCKS blocks that hold a nonzero block."""
+def tc_issued_flops(a_off, b_off, enc: dict) -> float:
+    """bf16 flops the tensor kernel issues for a batch (padding included): per tile of
+    32 tile_blocks outputs and per shift it meets (K-groups included), 2 MMAs of 128 x N x 16 with
+    N = tile_blocks * na, the tile's full width."""
+    nb_t = enc["tile_blocks"]
     n_all = np.diff(a_off)
     m_all = np.diff(b_off)
     tot = 0
@@ -340,17 +336,10 @@ def tc_issued_flops(a_off, b_off) -> float:
             n_, m_ = m_, n_
         na = (n_ + 31) // 32
         dmax = (m_ + 30) // 32
-        nblk = (n_ + m_ - 1 + 31) // 32
-        for t_ in range((n_ + m_ - 1 + 1535) // 1536):
-            I0 = 48 * t_
-            for d in range(max(0, I0 - na + 1), min(dmax, I0 + 47) + 1):
-                lo = max(I0, d)                      # first block of the tile this shift meets
-                hi = min(I0 + 47, d + na - 1, nblk - 1)  # last one
-                if hi < lo:
-                    continue
-                c0, c1 = (lo - I0) // TC_CHUNK_BLOCKS, (hi - I0) // TC_CHUNK_BLOCKS
-                tot += (c1 - c0 + 1) * 5 * TC_CHUNK_BLOCKS
-    return float(tot) * 2 * 2 * 128 * 16
+        for t_ in range((n_ + m_ - 1 + 32 * nb_t - 1) // (32 * nb_t)):
+            I0 = nb_t * t_
+            tot += min(dmax, I0 + nb_t - 1) - max(0, I0 - na + 1) + 1
+    return float(tot) * 2 * 2 * 128 * 16 * nb_t * enc["na"]
 
 
 def run_ours(args, world, rank, local):
@@ -444,8 +433,9 @@ def run_ours(args, world, rank, local):
         return 0
 
     pk, pk_kind = peaks()
-    achieved = MACS_T * FLOPS_PER_MAC / (ms_per_step * 1e-3) / 1e12
-    issued = tc_issued_flops(tp[1], tp[3]) / (ms_per_step * 1e-3) / 1e12
+    enc = pm.tensor_limbs()
+    achieved = MACS_T * 2 * enc["limb_products"] / (ms_per_step * 1e-3) / 1e12
+    issued = tc_issued_flops(tp[1], tp[3], enc) / (ms_per_step * 1e-3) / 1e12
     peak = pk["bf16_tflops"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -457,9 +447,12 @@ def run_ours(args, world, rank, local):
                      "frac": achieved / peak,
                      "peak_basis": f"measured bf16 dense GEMM, burst ({pk_kind}): the step is one short "
                                    "kernel timed alone",
-                     "achieved_basis": "useful work only: 20 bf16 limb products (40 flops) per modular MAC, "
-                                       "n*m MACs per pair, no tile padding; over the CUDA-event time of the "
-                                       "whole call (planning launch included)",
+                     "achieved_basis": f"useful work only: {enc['limb_products']} bf16 limb products "
+                                       f"({2 * enc['limb_products']} flops) per modular MAC ({enc['na']} balanced "
+                                       f"base-{enc['base_a']} limbs of a x {enc['nb']} base-{enc['base_b']} limbs "
+                                       "of b), n*m MACs per pair, no tile padding; over the CUDA-event time of "
+                                       "the whole call (planning launch included)",
+                     "encoding": enc,
                      "issued_tflops": issued, "issued_frac": issued / peak,
                      "kernel": "tc_batched_kernel",
                      "traffic": traffic_for("tc_batched_kernel", "tensor.cu", "common.cuh")},

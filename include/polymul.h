@@ -359,6 +359,22 @@ pm_status polymul_probe_mac_rate(int threads, int blocks_per_sm, int64_t iters, 
                                  void *stream);
 
 /*
+ * polymul_tensor_limbs - the limb encoding of the tensor-core form
+ * (polymul_batched with PM_TENSOR): a's coefficients, moved to the centred
+ * range (-p/2, p/2], are written as *na balanced base-*base_a digits in
+ * [-base_a/2, base_a/2), b's as *nb balanced base-*base_b digits; bf16 holds
+ * every digit exactly, and an fp32 accumulator entry sums at most *max_terms
+ * digit products, so its sums stay below 2^24 and exact (products whose
+ * shorter operand is longer run in K-groups of max_terms / 32 shifts).  One
+ * modular multiply-add costs na * nb bf16 limb products.  *tile_blocks is the
+ * tile width in blocks of 32 outputs (every MMA spans it: 128 rows by
+ * tile_blocks * na columns, two MMAs of K = 16 per shift of a tile).  Host
+ * only; no GPU needed.  Returns PM_OK or PM_ERR_INVALID_ARG (a null pointer).
+ */
+pm_status polymul_tensor_limbs(int *na, int *nb, uint32_t *base_a, uint32_t *base_b, int *max_terms,
+                               int *tile_blocks);
+
+/*
  * polymul_probe_mma - measures one tcgen05 MMA kind on this device, for the
  * limb encodings of the tensor-core form (PM_TENSOR): kind PM_MMA_BF16 is
  * kind::f16 with bf16 operands (K = 16), the one the product kernel issues;
@@ -379,19 +395,6 @@ pm_status polymul_probe_mac_rate(int threads, int blocks_per_sm, int64_t iters, 
  * captures), PM_ERR_TIMEOUT (a bounded wait of the probe ran out), PM_ERR_NOMEM
  * or PM_ERR_CUDA.
  */
-/*
- * polymul_tensor_limbs - the limb encoding of the tensor-core form
- * (polymul_batched with PM_TENSOR): a's coefficients, moved to the centred
- * range (-p/2, p/2], are written as *na balanced base-*base_a digits in
- * [-base_a/2, base_a/2), b's as *nb balanced base-*base_b digits; bf16 holds
- * every digit exactly, and an fp32 accumulator entry sums at most *max_terms
- * digit products, so its sums stay below 2^24 and exact (products whose
- * shorter operand is longer run in K-groups of max_terms / 32 shifts).  One
- * modular multiply-add costs na * nb bf16 limb products.  Host only; no GPU
- * needed.  Returns PM_OK or PM_ERR_INVALID_ARG (a null pointer).
- */
-pm_status polymul_tensor_limbs(int *na, int *nb, uint32_t *base_a, uint32_t *base_b, int *max_terms);
-
 #define PM_MMA_BF16 0
 #define PM_MMA_E4M3 1
 pm_status polymul_probe_mma(int kind, int64_t iters, double *flops_per_clk_sm, int *exact, void *stream);

@@ -1011,8 +1011,10 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
 
 }  // namespace pm
 
-extern "C" pm_status polymul_tensor_limbs(int* na, int* nb, uint32_t* base_a, uint32_t* base_b, int* max_terms) {
-    if (!na || !nb || !base_a || !base_b || !max_terms) return PM_ERR_INVALID_ARG;
+extern "C" pm_status polymul_tensor_limbs(int* na, int* nb, uint32_t* base_a, uint32_t* base_b, int* max_terms,
+                                          int* tile_blocks) {
+    if (!na || !nb || !base_a || !base_b || !max_terms || !tile_blocks) return PM_ERR_INVALID_ARG;
+    *tile_blocks = pm::NBLK;
     *na = pm::NA_LIMB;
     *nb = pm::NB_LIMB;
     *base_a = pm::BASE_A;

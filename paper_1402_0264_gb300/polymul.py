@@ -63,7 +63,7 @@ def _declare(lib):
         "polymul_probe_mac_rate": ([INT, INT, I64, ctypes.POINTER(D), V], INT),
         "polymul_probe_mma": ([INT, I64, ctypes.POINTER(D), ctypes.POINTER(INT), V], INT),
         "polymul_tensor_limbs": ([ctypes.POINTER(INT), ctypes.POINTER(INT), ctypes.POINTER(U32),
-                                  ctypes.POINTER(U32), ctypes.POINTER(INT)], INT),
+                                  ctypes.POINTER(U32), ctypes.POINTER(INT), ctypes.POINTER(INT)], INT),
         "polymul_tune_batched": ([I64, V, V, V, V, V, V, U32, I64, INT, V, ctypes.POINTER(INT),
                                   ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_float)], INT),
         "polymul_tune_save": ([ctypes.c_char_p], INT),
@@ -306,13 +306,13 @@ PM_MMA_BF16, PM_MMA_E4M3 = 0, 1
 
 def tensor_limbs() -> dict:
     """The tensor-core form's limb encoding (polymul_tensor_limbs): limbs and bases of a and b,
-    digit products per fp32 entry, limb products per modular MAC."""
-    na, nb, mt = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    digit products per fp32 entry, tile width in blocks of 32, limb products per modular MAC."""
+    na, nb, mt, tb = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
     ba, bb = ctypes.c_uint32(0), ctypes.c_uint32(0)
     _check(lib().polymul_tensor_limbs(ctypes.byref(na), ctypes.byref(nb), ctypes.byref(ba), ctypes.byref(bb),
-                                      ctypes.byref(mt)), "polymul_tensor_limbs")
+                                      ctypes.byref(mt), ctypes.byref(tb)), "polymul_tensor_limbs")
     return {"na": na.value, "nb": nb.value, "base_a": ba.value, "base_b": bb.value, "max_terms": mt.value,
-            "limb_products": na.value * nb.value}
+            "tile_blocks": tb.value, "limb_products": na.value * nb.value}
 
 
 def probe_mma(kind: int = PM_MMA_BF16, iters: int = 4096, stream=None) -> tuple[float, bool]:

@@ -53,33 +53,62 @@ def test_random_unequal_pairs():
 
 
 def _adversarial_values(p):
-    """Coefficients whose balanced digits are all at the extreme (-128 for b, -32 for a)."""
-    xb = p - 128 * (1 + 256 + 65536)        # digits (-128, -128, -128, 0) in base 256
-    xa = p - 32 * (1 + 64 + 4096 + 262144)  # digits (-32, -32, -32, -32, 0) in base 64
+    """Coefficients whose balanced digits are all at the extreme -B/2 below the top limb (top limb
+    0), for the encoding the library reports: every digit product is (B_a/2)(B_b/2), the largest
+    the encoding has."""
+    enc = pm.tensor_limbs()
+    ba, bb = enc["base_a"], enc["base_b"]
+    xa = p - (ba // 2) * sum(ba ** i for i in range(enc["na"] - 1))
+    xb = p - (bb // 2) * sum(bb ** i for i in range(enc["nb"] - 1))
     return xa, xb
 
 
-def test_worst_case_accumulation():
-    """Every product of digits is 4096 and 4096 terms meet: sums reach 2^24 exactly."""
-    xa, xb = _adversarial_values(P)
-    n = m = 4096
+def _worst_case(deg, p=P):
+    xa, xb = _adversarial_values(p)
+    n = m = deg + 1
     a = np.full(n, xa, np.uint32)
     b = np.full(m, xb, np.uint32)
     a_off = np.array([0, n], np.int64); b_off = np.array([0, m], np.int64)
     c_off = np.array([0, n + m - 1], np.int64)
-    packed = (a, a_off, b, b_off, c_off)
+    return a, a_off, b, b_off, c_off
+
+
+def test_adversarial_values_have_extreme_digits():
+    """The values above: centred, they are -(B/2)(1 + B + ... + B^(L-2)), whose balanced digits are
+    L-1 digits -B/2 and a top digit 0."""
+    enc = pm.tensor_limbs()
+    for x, base, limbs in zip(_adversarial_values(P), (enc["base_a"], enc["base_b"]), (enc["na"], enc["nb"])):
+        v = int(x) - P
+        u = v + (base // 2) * sum(base ** i for i in range(limbs))
+        digits = [(u // base ** i) % base - base // 2 for i in range(limbs)]
+        assert digits == [-(base // 2)] * (limbs - 1) + [0]
+        assert 0 <= u < base ** limbs
+
+
+def test_worst_case_accumulation():
+    """Every digit product is the largest the encoding has and an entry meets max_terms of them in one
+    accumulation (a pair of degree max_terms - 1, one K-group): the sums reach their bound (2^24 for
+    the encoding of 5 base-64 by 4 base-256 limbs)."""
+    deg = pm.tensor_limbs()["max_terms"] - 1
+    a, a_off, b, b_off, c_off = _worst_case(deg)
     want = oracle.polymul(a, b, P)
-    assert_equal(run(packed, 4095), want, "adversarial digits")
+    assert_equal(run((a, a_off, b, b_off, c_off), deg), want, "adversarial digits")
     # both operand orders, and all p-1
-    assert_equal(run((b, b_off, a, a_off, c_off), 4095), want, "swapped")
-    ones = np.full(n, P - 1, np.uint32)
-    assert_equal(run((ones, a_off, ones, b_off, c_off), 4095), oracle.polymul(ones, ones, P), "p-1")
+    assert_equal(run((b, b_off, a, a_off, c_off), deg), want, "swapped")
+    ones = np.full(deg + 1, P - 1, np.uint32)
+    assert_equal(run((ones, a_off, ones, b_off, c_off), deg), oracle.polymul(ones, ones, P), "p-1")
 
 
-@pytest.mark.parametrize("deg", [4096, 8191, 16383])
+def test_worst_case_accumulation_degree_4095():
+    """The headline degree with extreme digits (one K-group or several, by the encoding)."""
+    a, a_off, b, b_off, c_off = _worst_case(4095)
+    assert_equal(run((a, a_off, b, b_off, c_off), 4095), oracle.polymul(a, b, P), "adversarial digits")
+
+
+@pytest.mark.parametrize("deg", [2592, 4096, 8191, 16383])
 def test_degrees_beyond_one_k_group(deg):
-    """Pairs whose operands both exceed 4096 terms: each tile is accumulated in K-groups of at
-    most 128 shifts (4096 terms per entry) and the groups' residues added in the epilogue."""
+    """Pairs whose operands both exceed max_terms terms (for some encoding): each tile is accumulated
+    in K-groups of at most max_terms / 32 shifts and the groups' residues added in the epilogue."""
     packed = inputs.workload_tensor(batch=3, deg=deg, seed=inputs.SEED_BASE + 310 + deg)
     assert_equal(run(packed, deg), oracle.polymul_batch(*packed[:4], packed[4], P), f"deg {deg}")
 
@@ -94,14 +123,10 @@ def test_long_and_short_operands_beyond_4096():
 
 @pytest.mark.parametrize("deg", [8191, 16383])
 def test_worst_case_accumulation_in_k_groups(deg):
-    """Extreme digits at degrees 8191 and 16383: a K-group's sums reach 2^24 exactly, and the groups
+    """Extreme digits at degrees 8191 and 16383: a K-group's sums reach their bound, and the groups
     of a tile are added mod p."""
-    xa, xb = _adversarial_values(P)
+    a, a_off, b, b_off, c_off = _worst_case(deg)
     n = m = deg + 1
-    a = np.full(n, xa, np.uint32)
-    b = np.full(m, xb, np.uint32)
-    a_off = np.array([0, n], np.int64); b_off = np.array([0, m], np.int64)
-    c_off = np.array([0, n + m - 1], np.int64)
     want = oracle.ntt_polymul(a, b, P)
     assert_equal(run((a, a_off, b, b_off, c_off), deg), want, "adversarial digits")
     assert_equal(run((b, b_off, a, a_off, c_off), deg), want, "swapped")
