@@ -5,30 +5,33 @@
 // exact small-integer matrix products.
 //
 // Limbs.  Coefficients are first moved to the centred range (-p/2, p/2]
-// (same residue).  b is split into 4 balanced base-256 digits d_j in
-// [-128, 127], a into 5 balanced base-64 digits e_i in [-32, 31]; bf16 holds
-// both exactly.  Then
-//     c = sum_{i<5, j<4} 64^i 256^j (e_i * d_j)   (mod p),
+// (same residue, |v| < 2^28 for p < 2^29) and written as 4 balanced base-160
+// digits in [-80, 79]: d_j for b, e_i for a (an offset K = 80 (1 + 160 +
+// 160^2 + 160^3) makes v + K a standard base-160 number below 160^4); bf16
+// holds them exactly.  Then
+//     c = sum_{i<4, j<4} 160^i 160^j (e_i * d_j)   (mod p),
 // and every entry of a digit convolution e_i * d_j accumulated over a group of
-// shifts is a sum of products of magnitude <= 128 * 32 = 2^12, one for each
+// shifts is a sum of products of magnitude <= 80 * 80 = 6400, one for each
 // index of b the group's shifts reach (at most min(n, m), and at most 32 per
-// shift): with at most 4096 terms it stays within 2^24 in magnitude and the
+// shift): with at most 2592 terms it stays below 2^24 in magnitude and the
 // tensor core's fp32 accumulation is exact.  A tile whose shifts reach more
-// than 4096 indices of both operands (min(n, m) > 4096) is done in K-groups of
-// at most 128 shifts, each accumulated on its own and reduced mod p, the
-// later groups added onto the earlier groups' residues in the epilogue.
-// (tcgen05 kind::i8 would hold larger limbs, but ptxas rejects it for
-// sm_103a.)
+// than 2592 indices of both operands (min(n, m) > 2592) is done in K-groups of
+// at most 81 shifts, each accumulated on its own and reduced mod p, the later
+// groups added onto the earlier groups' residues in the epilogue.  16 limb
+// products per modular MAC.  (The build option PM_TC_ENC=0 keeps the earlier
+// encoding: 5 base-64 digits of a in [-32, 31] x 4 base-256 digits of b, 20
+// limb products, 4096 terms per group, tiles of 48 blocks.  tcgen05 kind::i8
+// would hold larger limbs, but ptxas rejects it for sm_103a.)
 //
 // Matrix form (T = 32 outputs per block, block I covers outputs 32 I .. 32 I + 31;
 // the K index runs backwards, k' = 31 - k, in both operands):
 //     D[(j, r)][(I, i)] = sum_delta sum_{k'<32} d_j[32 delta - 31 + r + k'] * e_i[32 (I - delta) + 31 - k']
 //                       = (e_i * d_j)[32 I + r].
-// For one shift delta this is one 128 x 240 x 32 product (two MMAs of K = 16):
-// N = 240 columns are 48 output blocks times the 5 limbs of a; the a operand
+// For one shift delta this is one 128 x 256 x 32 product (two MMAs of K = 16):
+// N = 256 columns are 64 output blocks times the 4 limbs of a; the a operand
 // is stored once per tile as rows (J, i) = limb i of block J of a, reversed,
-// and the rows shift delta needs are the same rows moved by 5 per delta, so
-// its descriptor just starts 5 * 16 bytes earlier for each delta.  M = 128
+// and the rows shift delta needs are the same rows moved by 4 per delta, so
+// its descriptor just starts 4 * 16 bytes earlier for each delta.  M = 128
 // rows are the 4 limbs of b times 32 offsets r, ordered (r / 8, limb j, r mod 8)
 // so that one descriptor covers all limbs: with k' reversed, the 8 x 8 core
 // matrix of limb j at row group r / 8 = g and K chunk c holds
@@ -38,14 +41,17 @@
 // descriptor walks them with 128 bytes between row groups (the next limb or,
 // after 4 limbs, the next g) and 512 bytes between K chunks (the next q).  A
 // shift thus costs 4 new core matrices per limb instead of a 128 x 32 block.
-// All shifts accumulate into one TMEM tile (240 fp32 columns x 128 lanes).
+// All shifts of a K-group accumulate into one TMEM tile (256 fp32 columns x
+// 128 lanes); two such tiles alternate.  Every MMA spans the full width: the
+// time of an MMA here hardly shrinks with N (N = 192 measured no faster than
+// 240), so the widest tile that TMEM holds twice issues the fewest MMAs.
 //
 // Epilogue.  TMEM lane 32 g + 8 j + t holds D[(j, 8 g + t)][.]: warp g reads
-// its 32 lanes, each thread forms sum_i 64^i D (exact in int64), reduces it
-// mod p and multiplies by 256^j mod p, and the 4 limbs of one output are
+// its 32 lanes, each thread forms sum_i 160^i D (exact in int64), reduces it
+// mod p and multiplies by 160^j mod p, and the 4 limbs of one output are
 // added with two warp shuffles before the store.
 //
-// Work: tiles of 1536 outputs of every pair, taken by persistent CTAs (one
+// Work: tiles of 2048 outputs of every pair, taken by persistent CTAs (one
 // per SM) from an atomic counter; the K-groups of a tile run one after the
 // other on the CTA that took it.  Every wait on an mbarrier is bounded: when
 // it runs out the kernel records PM_ERR_TIMEOUT and skips the remaining work.
@@ -64,7 +70,7 @@ constexpr int TT = 32;                     // outputs per block
 // Limb encoding (build-time choice): 1 = 4 balanced base-160 limbs of each operand (16
 // limb products per modular MAC), 0 = 5 base-64 limbs of a x 4 base-256 limbs of b (20).
 #ifndef PM_TC_ENC
-#define PM_TC_ENC 0
+#define PM_TC_ENC 1
 #endif
 #if PM_TC_ENC == 1
 constexpr int NA_LIMB = 4, NB_LIMB = 4;
@@ -78,12 +84,12 @@ constexpr int TC_MAXK = 4096;   // 4096 * 32 * 128 = 2^24
 static_assert((int64_t)TC_MAXK * (BASE_A / 2) * (BASE_B / 2) <= (1 << 24), "fp32 sums stay exact");
 static_assert(NB_LIMB == 4, "M = 128 rows: 4 limbs of b x 32 offsets");
 #ifndef PM_TC_NBLK
-#define PM_TC_NBLK 48  // output blocks per tile (a multiple of 16)
+#define PM_TC_NBLK (PM_TC_ENC == 1 ? 64 : 48)  // output blocks per tile (a multiple of 16)
 #endif
 constexpr int NBLK = PM_TC_NBLK;           // blocks per tile
-constexpr int MMA_M = 128, MMA_N = NBLK * NA_LIMB;  // 192 (4 limbs of a) or 240 (5)
+constexpr int MMA_M = 128, MMA_N = NBLK * NA_LIMB;  // 256 (64 blocks x 4 limbs of a) or 240 (48 x 5)
 static_assert(NBLK % 16 == 0 && MMA_N <= 256, "tile width");
-constexpr int TILE_OUT = TT * NBLK;        // 1536
+constexpr int TILE_OUT = TT * NBLK;        // 2048 (or 1536)
 constexpr int TC_GROUP = TC_MAXK / TT;     // shifts per K-group when both operands are longer
 constexpr int64_t TC_MAX_DEG = PM_TENSOR_MAX_DEG;      // degrees this path takes (int tile indices)
 constexpr int GROUP_D = 8;                 // shifts per Hankel slot
@@ -99,7 +105,7 @@ constexpr int B_LBO = ROWS_MAX * 16;                   // bytes between K chunks
 constexpr int B_BUF = 4 * B_LBO;                       // one a operand (double-buffered across tiles)
 constexpr int H_Q = 4 * GROUP_D + 4;                   // Hankel core-matrix indices per slot (4 G + 3 used)
 constexpr int H_SLOT = H_Q * 512;                      // 4 limbs x 128-byte core matrices per index
-constexpr uint32_t TMEM_COLS = 512;                    // two accumulators of 240 columns
+constexpr uint32_t TMEM_COLS = 512;                    // two accumulators of MMA_N columns
 constexpr uint32_t ACC_STRIDE = 256;
 constexpr int64_t WAIT_LIMIT = 1ll << 26;              // polls before a wait is declared lost (default)
 static_assert((BDS / 2) % 32 == 8, "limb stride must spread the limbs over the banks");
@@ -645,7 +651,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
     } else {
         // ---------------- epilogue ----------------
         // warp w reads TMEM lanes 32 (w % 4) .. + 31 = (limb j, offset 8 (w % 4) + t) and
-        // half of the columns (24 blocks); the 4 limbs of an output sit on lanes t, t + 8,
+        // half of the columns (NBLK / 2 blocks); the 4 limbs of an output sit on lanes t, t + 8,
         // t + 16, t + 24 and are combined by a reduce-scatter over 4 blocks at a time.
         const int quarter = warp & 3, half = (warp - EPI_WARP0) >> 2;
         const int j = lane >> 3, r = 8 * quarter + (lane & 7);

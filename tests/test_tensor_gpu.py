@@ -29,8 +29,8 @@ def run(packed, max_deg, p=P, mode=pm.PM_TENSOR):
 
 
 def test_small_ragged_batch():
-    da = np.array([0, 1, 5, 31, 32, 33, 1000, 1535, 1536, 2047, 4095, 17], np.int64)
-    db = np.array([0, 3, 5, 32, 31, 33, 17, 1536, 1535, 2047, 4095, 4000], np.int64)
+    da = np.array([0, 1, 5, 31, 32, 33, 1000, 1535, 1536, 2047, 4095, 17, 1024, 2049, 2591], np.int64)
+    db = np.array([0, 3, 5, 32, 31, 33, 17, 1536, 1535, 2047, 4095, 4000, 1025, 2048, 2592], np.int64)
     packed = inputs.packed_batch(da, db, 91)
     assert_equal(run(packed, 4095), oracle.polymul_batch(*packed[:4], packed[4], P))
 
