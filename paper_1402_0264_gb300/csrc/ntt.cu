@@ -387,6 +387,19 @@ __device__ __forceinline__ void col_transform(uint32_t* sh, const uint2* __restr
 __device__ __forceinline__ int rphys(int i) { return i + (i >> 4); }
 constexpr int ROW_WORDS = NTT_N2 + NTT_N2 / 16;
 
+// Twiddles of the row transforms (w = w_N2 forward, w_N2^-1 inverse), stored in the
+// order the threads read them, so that a warp's load of one twiddle is one or two
+// contiguous 128-byte lines (read by exponent, the second level of stage 1 and both
+// levels of stage 2 would touch 8 to 24 lines per load):
+//   A1[k][e]      = w^(k e),                e < 1024    stage 1, first level (e = t + 256 l0)
+//   B1[k][t]      = w^(4 k t),              t < 256     stage 1, second level
+//   A2[k][l0][tp] = w^(k (16 tp + 256 l0)), l0 < 4, tp < 16   stage 2, first level
+//   B2[k][tp]     = w^(64 k tp),            tp < 16     stage 2, second level
+// for k = 1, 2, 3 (stored at k - 1).
+constexpr int RT_A1 = 0, RT_B1 = RT_A1 + 3 * 1024, RT_A2 = RT_B1 + 3 * 256, RT_B2 = RT_A2 + 3 * 64;
+constexpr int RT_WORDS = RT_B2 + 3 * 16;
+static_assert(RT_WORDS <= NTT_N2, "row twiddles fit the table slot");
+
 // row_stage on NR arrays at once (the forward transforms of a's and b's rows): every
 // twiddle is loaded once for all of them; stage 3's come from the kernel parameters.
 template <bool FWD, int NR>
@@ -401,9 +414,10 @@ __device__ __forceinline__ void row_stage_n(int stage, uint32_t (*rs[NR])[16], u
             if (stage == 3) {
                 on = l0 != 0;
                 a1 = c3[l0 ? l0 - 1 : 0][0]; a2 = c3[l0 ? l0 - 1 : 0][1]; a3 = c3[l0 ? l0 - 1 : 0][2];
-            } else {  // (e = 0 on some lanes: multiplied by entry 0 = 1, so no lane diverges)
-                const int e = stage == 1 ? t + 256 * l0 : 16 * (tp + 16 * l0);
-                a1 = __ldg(tw + e); a2 = __ldg(tw + 2 * e); a3 = __ldg(tw + 3 * e);
+            } else {  // (exponent 0 on some lanes: multiplied by w^0 = 1, so no lane diverges)
+                const uint2* q = stage == 1 ? tw + RT_A1 + t + 256 * l0 : tw + RT_A2 + 16 * l0 + tp;
+                const int ks = stage == 1 ? 1024 : 64;  // stride between k = 1, 2, 3
+                a1 = __ldg(q); a2 = __ldg(q + ks); a3 = __ldg(q + 2 * ks);
             }
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
@@ -413,11 +427,14 @@ __device__ __forceinline__ void row_stage_n(int stage, uint32_t (*rs[NR])[16], u
         }
     };
     auto lvB = [&]() {
-        // stages 1 and 2: per-lane exponents (entry 0 = 1 where e = 0); stage 3: none for any lane
-        const int e = stage == 1 ? 4 * t : stage == 2 ? 64 * tp : 0;
+        // stages 1 and 2: per-lane exponents (w^0 = 1 where it is 0); stage 3: none for any lane
         const bool on = stage != 3;
         uint2 a1 = make_uint2(0, 0), a2 = a1, a3 = a1;
-        if (on) { a1 = __ldg(tw + e); a2 = __ldg(tw + 2 * e); a3 = __ldg(tw + 3 * e); }
+        if (on) {
+            const uint2* q = stage == 1 ? tw + RT_B1 + t : tw + RT_B2 + tp;
+            const int ks = stage == 1 ? 256 : 16;
+            a1 = __ldg(q); a2 = __ldg(q + ks); a3 = __ldg(q + 2 * ks);
+        }
 #pragma unroll
         for (int l1 = 0; l1 < 4; ++l1)
 #pragma unroll
@@ -437,10 +454,10 @@ __device__ __forceinline__ int row_index(int stage, int t, int l) {
 // Device tables of one (p, g, log N), each entry (w, floor(w 2^32 / p)).
 struct NttTables {
     const uint2 *lo, *ilo;    // w_N^e, w_N^-e, e < 4096
-    const uint2 *row, *irow;  // w_N2^e, w_N2^-e, e < 4096 (N > 4096)
+    const uint2 *row, *irow;  // twiddles of the row transforms (w_N2, w_N2^-1) in thread order: see RT_A1
     const uint2 *hi, *ihi;    // w_N^(4096 f), w_N^(-4096 f), f < N1 (= w_N1^f)
     uint2 scale;              // N^-1 2^32 mod p
-    uint32_t w4_unused;
+    uint2 rw4, riw4;          // w_N2^(N2/4), w_N2^-(N2/4)
     // the twiddles of the row transforms' third stage, the same for every thread:
     // st3[l0 - 1][k - 1] = w_N2^(256 l0 k) (ist3: w_N2^-(256 l0 k)), l0, k = 1..3
     uint2 st3[3][3], ist3[3][3];
@@ -452,6 +469,13 @@ __device__ __forceinline__ uint32_t mul_root_lz(uint32_t x, uint32_t e, const ui
                                                 uint32_t p) {
     return mul_shoup_lz(mul_shoup_lz(x, __ldg(lo + (e & (NTT_N2 - 1))), p), __ldg(hi + (e >> NTT_N2_LOG)), p);
 }
+// (w_N^e, floor(w_N^e 2^32 / p)) for e < N from the same two tables (canonical product, then its
+// Shoup quotient)
+__device__ __forceinline__ uint2 root_pair(uint32_t e, const uint2* lo, const uint2* hi, uint32_t p) {
+    const uint32_t w = mul_shoup(__ldg(lo + (e & (NTT_N2 - 1))).x, __ldg(hi + (e >> NTT_N2_LOG)), p);
+    return make_uint2(w, (uint32_t)(((uint64_t)w << 32) / p));
+}
+
 // ---- N <= 4096: one CTA per product ----
 __global__ void __launch_bounds__(NTT_THREADS) ntt_small_kernel(
     const uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ b, int m,
@@ -526,7 +550,13 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
     pdl_trigger();
     if (!PM_CHK(blockIdx.x < (1u << logn1) && blockDim.x == 256)) return;  // (uniform: before any barrier)
     const uint32_t p = md.p;
-    const uint2 w4 = __ldg(tb.row + NTT_N2 / 4), iw4 = __ldg(tb.irow + NTT_N2 / 4);
+    const uint2 w4 = tb.rw4, iw4 = tb.riw4;
+    const uint32_t k1 = freq_of_pos_fast(blockIdx.x, logn1);
+    const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
+    // the final twist by w_N^-(i k1), i = t + 256 l, as w_N^-(256 l k1) (one per l, for the whole
+    // CTA: sC, read after the barriers below) times w_N^-(t k1) (one per thread)
+    __shared__ uint2 sC[16];
+    if (t < 16) sC[t] = root_pair((uint32_t)((256ull * t * k1) & nmask), tb.ilo, tb.ihi, p);
     uint32_t r[16], q[16];
     // stage 1 of both rows, straight from global memory
 #pragma unroll
@@ -579,14 +609,9 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[l] = sA[rphys(t + 256 * l)];
     row_stage_n<false, 1>(1, ro, iw4, tb.irow, tb.ist3, p);
-    const uint32_t k1 = freq_of_pos_fast(blockIdx.x, logn1);
-    const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
+    const uint2 bt = root_pair((uint32_t)(((uint64_t)t * k1) & nmask), tb.ilo, tb.ihi, p);
 #pragma unroll
-    for (int l = 0; l < 16; ++l) {
-        const int i = t + 256 * l;
-        const uint32_t e = (uint32_t)(((uint64_t)i * k1) & nmask);
-        ta[r0 + i] = mul_root_lz(r[l], e, tb.ilo, tb.ihi, p);
-    }
+    for (int l = 0; l < 16; ++l) ta[r0 + t + 256 * l] = mul_shoup_lz(mul_shoup_lz(r[l], sC[l], p), bt, p);
 }
 
 // ---- four-step pass 3: inverse column transforms, scale, store ----
@@ -683,8 +708,22 @@ static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStrea
     for (int e = 0; e < NTT_N2; ++e) {
         lo[e] = shoup_pair(powmod_h(w, (uint64_t)e % N, p), p);
         ilo[e] = shoup_pair(powmod_h(wi, (uint64_t)e % N, p), p);
-        row[e] = shoup_pair(powmod_h(w, ((uint64_t)n1 * e) % N, p), p);
-        irow[e] = shoup_pair(powmod_h(wi, ((uint64_t)n1 * e) % N, p), p);
+    }
+    if (logn > NTT_N2_LOG) {  // the row transforms' twiddles in thread order (RT_A1 ...)
+        const uint32_t w2 = powmod_h(w, (uint64_t)n1, p), w2i = powmod_h(wi, (uint64_t)n1, p);  // w_N2, w_N2^-1
+        auto fill = [&](uint2* T, uint32_t base) {
+            auto pw = [&](uint64_t x) { return shoup_pair(powmod_h(base, x % NTT_N2, p), p); };
+            for (int k = 1; k <= 3; ++k) {
+                for (int e = 0; e < 1024; ++e) T[RT_A1 + (k - 1) * 1024 + e] = pw((uint64_t)k * e);
+                for (int t = 0; t < 256; ++t) T[RT_B1 + (k - 1) * 256 + t] = pw(4ull * k * t);
+                for (int l0 = 0; l0 < 4; ++l0)
+                    for (int tp = 0; tp < 16; ++tp)
+                        T[RT_A2 + ((k - 1) * 4 + l0) * 16 + tp] = pw((uint64_t)k * (16 * tp + 256 * l0));
+                for (int tp = 0; tp < 16; ++tp) T[RT_B2 + (k - 1) * 16 + tp] = pw(64ull * k * tp);
+            }
+        };
+        fill(row, w2);
+        fill(irow, w2i);
     }
     for (int f = 0; f < n1; ++f) {
         hi[f] = shoup_pair(powmod_h(w, ((uint64_t)NTT_N2 * f) % N, p), p);
@@ -717,6 +756,8 @@ static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStrea
                 ts.t.st3[l0 - 1][k - 1] = shoup_pair(powmod_h(w2, (uint64_t)(256 * l0 * k), p), p);
                 ts.t.ist3[l0 - 1][k - 1] = shoup_pair(powmod_h(w2i, (uint64_t)(256 * l0 * k), p), p);
             }
+        ts.t.rw4 = shoup_pair(powmod_h(w2, NTT_N2 / 4, p), p);
+        ts.t.riw4 = shoup_pair(powmod_h(w2i, NTT_N2 / 4, p), p);
     }
     g_tables[key] = ts;
     *out = ts.t;
