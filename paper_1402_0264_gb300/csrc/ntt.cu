@@ -456,6 +456,7 @@ struct NttTables {
     const uint2 *lo, *ilo;    // w_N^e, w_N^-e, e < 4096
     const uint2 *row, *irow;  // twiddles of the row transforms (w_N2, w_N2^-1) in thread order: see RT_A1
     const uint2 *hi, *ihi;    // w_N^(4096 f), w_N^(-4096 f), f < N1 (= w_N1^f)
+    const uint2 *tj;          // w_N^(j k1) at k1 * cols + j, k1 < N1, j < cols (the column block width)
     uint2 scale;              // N^-1 2^32 mod p
     uint2 rw4, riw4;          // w_N2^(N2/4), w_N2^-(N2/4)
     // the twiddles of the row transforms' third stage, the same for every thread:
@@ -528,13 +529,17 @@ __global__ void __launch_bounds__(NTT_THREADS, NTT_COL_MINB) ntt_col_fwd_kernel(
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     col_transform<true, COLS, LOG1>(sh, tb.hi, md.p);
-    constexpr uint64_t nmask = ((((uint64_t)1) << LOG1) << NTT_N2_LOG) - 1;
+    // the twist w_N^((c0 + j) k1) = w_N^(c0 k1) (two table factors, one pair per position: 4 per
+    // warp) times w_N^(j k1) (tb.tj, j fastest: 4 runs of COLS entries per warp), so that a warp's
+    // loads touch 4 lines each; (c0 + j) k1 < 4096 N1 = N, so no exponent wraps
 #pragma unroll 4
     for (int idx = threadIdx.x; idx < COLS * N1; idx += NTT_THREADS) {
         const int j = idx % COLS, pos = idx / COLS;
         const uint32_t k1 = freq_of_pos_fast((uint32_t)pos, LOG1);
-        const uint32_t e = (uint32_t)(((uint64_t)(c0 + j) * k1) & nmask);
-        out[(size_t)pos * NTT_N2 + c0 + j] = mul_root_lz(sh[cphys(pos) * COLS + j], e, tb.lo, tb.hi, md.p);
+        const uint32_t e0 = (uint32_t)c0 * k1;
+        const uint32_t x = mul_shoup_lz(sh[cphys(pos) * COLS + j], __ldg(tb.lo + (e0 & (NTT_N2 - 1))), md.p);
+        out[(size_t)pos * NTT_N2 + c0 + j] =
+            mul_shoup_lz(mul_shoup_lz(x, __ldg(tb.hi + (e0 >> NTT_N2_LOG)), md.p), __ldg(tb.tj + k1 * COLS + j), md.p);
     }
 }
 
@@ -697,7 +702,8 @@ static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStrea
     if (N >= 2 && powmod_h(w, N / 2, p) != p - 1) return PM_ERR_UNSUPPORTED;  // not of order N
     const uint32_t wi = powmod_h(w, p - 2, p);
     const int n1 = logn > NTT_N2_LOG ? (int)(N >> NTT_N2_LOG) : 1;
-    const size_t words = 4 * NTT_N2 + 2 * (size_t)n1;
+    const int tcols = logn > NTT_N2_LOG ? ColTable::cols[logn - NTT_N2_LOG - 1] : 0;  // columns per block
+    const size_t words = 4 * NTT_N2 + 2 * (size_t)n1 + (size_t)tcols * n1;
     std::vector<uint2> h(words);
     uint2* lo = h.data();
     uint2* ilo = lo + NTT_N2;
@@ -705,6 +711,9 @@ static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStrea
     uint2* irow = row + NTT_N2;
     uint2* hi = irow + NTT_N2;
     uint2* ihi = hi + n1;
+    uint2* tj = ihi + n1;
+    for (int k1 = 0; k1 < (tcols ? n1 : 0); ++k1)
+        for (int j = 0; j < tcols; ++j) tj[(size_t)k1 * tcols + j] = shoup_pair(powmod_h(w, ((uint64_t)j * k1) % N, p), p);
     for (int e = 0; e < NTT_N2; ++e) {
         lo[e] = shoup_pair(powmod_h(w, (uint64_t)e % N, p), p);
         ilo[e] = shoup_pair(powmod_h(wi, (uint64_t)e % N, p), p);
@@ -745,6 +754,7 @@ static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStrea
     ts.t.irow = ts.dev + 3 * NTT_N2;
     ts.t.hi = ts.dev + 4 * NTT_N2;
     ts.t.ihi = ts.t.hi + n1;
+    ts.t.tj = ts.t.ihi + n1;
     // N^-1 * 2^32 mod p cancels the Montgomery factor of the pointwise product
     const uint32_t ninv = powmod_h(N % p, p - 2, p);
     const uint32_t r32 = (uint32_t)((1ull << 32) % p);
