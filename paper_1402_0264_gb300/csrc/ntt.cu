@@ -315,7 +315,9 @@ __device__ __forceinline__ void col_stage(uint32_t* sh, const uint2* __restrict_
 #pragma unroll
             for (int ks = 0; ks < RS; ++ks) {
                 const int jl = j + (ks << LG_SS);
-                if constexpr (RL == 4) {
+                if constexpr (RL == 4 && RS == 1 && LG_SL == 0) {  // a single level of span 1: no twiddles
+                    bf4t<FWD>(r[ks], r[ks + RS], r[ks + 2 * RS], r[ks + 3 * RS], w4, w4, w4, w4, false, p);
+                } else if constexpr (RL == 4) {
                     const int e = jl << (LOGM - 2 - LG_SL);
                     bf4<FWD>(r[ks], r[ks + RS], r[ks + 2 * RS], r[ks + 3 * RS], w4, tw, e, p);
                 } else {
@@ -323,9 +325,14 @@ __device__ __forceinline__ void col_stage(uint32_t* sh, const uint2* __restrict_
                 }
             }
         };
-        // the level of span s_small (radix 4): offset j in its blocks
+        // the level of span s_small (radix 4): offset j in its blocks (span 1: j = 0, every twiddle
+        // is w^0 = 1 and the butterflies take none)
         auto small = [&]() {
-            if constexpr (RS == 4) {
+            if constexpr (RS == 4 && LG_SS == 0) {
+#pragma unroll
+                for (int kl = 0; kl < RL; ++kl)
+                    bf4t<FWD>(r[RS * kl], r[RS * kl + 1], r[RS * kl + 2], r[RS * kl + 3], w4, w4, w4, w4, false, p);
+            } else if constexpr (RS == 4) {
                 const int e = j << (LOGM - 2 - LG_SS);
 #pragma unroll
                 for (int kl = 0; kl < RL; ++kl) bf4<FWD>(r[RS * kl], r[RS * kl + 1], r[RS * kl + 2], r[RS * kl + 3], w4, tw, e, p);
