@@ -190,6 +190,33 @@ pm_status polymul_batched(int64_t batch, const uint32_t *a_data, const int64_t *
                           int mode, int s, int64_t max_deg, void *stream);
 
 /*
+ * polymul_batched_host - polymul_batched from and to HOST buffers: the same
+ * arguments, with a_data, a_off, b_data, b_off, c_data and c_off in host
+ * memory (page-locked memory, cudaHostAlloc / cudaHostRegister, lets the
+ * copies run asynchronously and overlap; pageable memory works, slower).  The
+ * batch is cut into up to 4 chunks of consecutive pairs with about equal
+ * multiply-adds; each chunk's words are copied to the device, multiplied by
+ * polymul_batched (same mode, s and max_deg) and copied back, on three streams
+ * of the library's own (per device), so that the copies of one chunk overlap
+ * the products of the next.  Stream order: the copies start after the work
+ * queued on `stream` before the call, and work queued on `stream` after it
+ * runs once every product is back in c_data; the host buffers must stay
+ * valid, and the inputs unchanged, until then.  The device buffers (two chunk
+ * slots) are the library's, grown when a larger chunk needs it and freed by
+ * polymul_release.  The offsets are checked on the host (the same layout rules
+ * as polymul_batched; PM_ERR_INVALID_ARG), and c_data may not overlap a_data
+ * or b_data.  Not capturable: returns PM_ERR_UNSUPPORTED while `stream`
+ * captures.  (No counterpart in the paper: the end-to-end form of the batched
+ * product.)
+ * Returns PM_OK, PM_ERR_INVALID_ARG, PM_ERR_RANGE, PM_ERR_UNSUPPORTED,
+ * PM_ERR_NOMEM or PM_ERR_CUDA; kernel-side errors go to the status word.
+ */
+pm_status polymul_batched_host(int64_t batch, const uint32_t *a_data, const int64_t *a_off,
+                               const uint32_t *b_data, const int64_t *b_off, uint32_t *c_data,
+                               const int64_t *c_off, uint32_t p, int mode, int s, int64_t max_deg,
+                               void *stream);
+
+/*
  * polymul_divide - Euclidean division over Z/pZ (Section 3, "Polynomial
  * division", Algorithms 3-4 with parameter s; s = 1 is the naive division of
  * Algorithms 1-2): the unique q and r with a = q b + r and deg r < deg b.

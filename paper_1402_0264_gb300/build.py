@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpolymul.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "plain.cu", "plain_ell.cu", "ntt.cu", "tensor.cu", "div.cu", "gcd.cu", "probe.cu", "tune.cu"]
+SOURCES = ["api.cu", "plain.cu", "plain_ell.cu", "ntt.cu", "tensor.cu", "div.cu", "gcd.cu", "probe.cu", "tune.cu",
+           "hostio.cu"]
 DEPS = {"plain_ell.cu": ["plain.cu"]}  # sources that include another source
 
 

@@ -537,6 +537,7 @@ pm_status polymul_sync_status(void* stream) {
 }
 
 pm_status polymul_release(void) {
+    release_host_io();
     release_ntt_tables();
     std::lock_guard<std::mutex> lock(g_ws_mutex);
     int cur = 0;

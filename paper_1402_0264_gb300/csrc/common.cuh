@@ -157,6 +157,7 @@ cudaError_t dev_alloc(void** ptr, size_t bytes);
 // limit (polymul_debug_set(PM_DEBUG_TC_WAIT_LIMIT, k)).
 int64_t tc_wait_limit();
 void release_ntt_tables();
+void release_host_io();
 void count_launches(uint64_t k);
 bool is_capturing(void* stream);
 

@@ -48,6 +48,7 @@ def _declare(lib):
         "polymul_plain_noalloc": ([V, I64, V, I64, V, U32, INT, V], INT),
         "polymul_plain_ell": ([V, I64, V, I64, V, U32, INT, INT, V], INT),
         "polymul_batched": ([I64, V, V, V, V, V, V, U32, INT, INT, I64, V], INT),
+        "polymul_batched_host": ([I64, V, V, V, V, V, V, U32, INT, INT, I64, V], INT),
         "polymul_divide": ([V, I64, V, I64, V, V, U32, INT, V], INT),
         "polymul_gcd": ([V, I64, V, I64, V, ctypes.POINTER(I64), U32, INT, V], INT),
         "polymul_model_predict": ([I64, I64, INT, INT, D, D, ctypes.POINTER(D)], INT),
@@ -185,6 +186,43 @@ def batched(a_data, a_off, b_data, b_off, c_off, max_deg: int, p: int = P_DEFAUL
                                  _dev_words(b_data, "b_data"), _dev_i64(b_off, "b_off"),
                                  _dev_words(out, "out"), _dev_i64(c_off, "c_off"), p, mode, s,
                                  max_deg, _stream_ptr(stream)), "polymul_batched")
+    return out
+
+
+def _host_array(t, name: str, itemsize: int):
+    """(pointer, length) of a contiguous 1-D host array: a CPU tensor (pinned for overlapped
+    copies) or a numpy array."""
+    torch = _torch()
+    if isinstance(t, torch.Tensor):
+        if t.is_cuda or t.element_size() != itemsize or not t.is_contiguous() or t.dim() != 1:
+            raise TypeError(f"{name} must be a contiguous 1-D CPU tensor of {8 * itemsize}-bit words")
+        return ctypes.c_void_p(t.data_ptr()), t.numel()
+    import numpy as np
+    if not isinstance(t, np.ndarray) or t.itemsize != itemsize or t.ndim != 1 or not t.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"{name} must be a contiguous 1-D array of {8 * itemsize}-bit words")
+    return ctypes.c_void_p(t.ctypes.data), t.size
+
+
+def batched_host(a_data, a_off, b_data, b_off, c_off, out, max_deg: int, p: int = P_DEFAULT,
+                 mode: int = PM_PLAIN, s: int = 0, stream=None):
+    """polymul_batched_host: the products of a CSR batch whose arrays are all in host memory (CPU
+    tensors or numpy arrays; pinned CPU tensors let the copies overlap the products).  `out` (host,
+    c_off[-1] words) holds the products once `stream` has reached the call's end."""
+    pa, na = _host_array(a_data, "a_data", 4)
+    pao, nao = _host_array(a_off, "a_off", 8)
+    pb, nb = _host_array(b_data, "b_data", 4)
+    pbo, nbo = _host_array(b_off, "b_off", 8)
+    pco, nco = _host_array(c_off, "c_off", 8)
+    pc, nc = _host_array(out, "out", 4)
+    batch = nao - 1
+    if nbo != nao or nco != nao:
+        raise ValueError("the three offset arrays must have batch + 1 entries")
+    if batch > 0:
+        last = [int(x[-1]) for x in (a_off, b_off, c_off)]
+        if last[0] > na or last[1] > nb or last[2] > nc:
+            raise ValueError("an offset array points past its data array")
+    _check(lib().polymul_batched_host(batch, pa, pao, pb, pbo, pc, pco, p, mode, s, max_deg, _stream_ptr(stream)),
+           "polymul_batched_host")
     return out
 
 

@@ -57,6 +57,24 @@ def test_probe_validation_happens_on_host(lib):
     assert g(256, 0, 100, ctypes.byref(r), NULL) == 1
 
 
+def test_batched_host_validation_happens_on_host(lib):
+    """The host-buffer batch checks its offsets and the output's overlap on the host, before any
+    device work."""
+    import numpy as np
+    a = np.ones(8, np.uint32); b = np.ones(8, np.uint32); c = np.zeros(15, np.uint32)
+    a_off = np.array([0, 8], np.int64); b_off = np.array([0, 8], np.int64); c_off = np.array([0, 15], np.int64)
+    f = lib.polymul_batched_host
+    ptr = lambda x: ctypes.c_void_p(x.ctypes.data)
+    bad_c = np.array([0, 14], np.int64)                       # product length != n + m - 1
+    assert f(1, ptr(a), ptr(a_off), ptr(b), ptr(b_off), ptr(c), ptr(bad_c), pm.P_DEFAULT, pm.PM_PLAIN, 0, 7, NULL) == 1
+    assert f(1, ptr(a), ptr(a_off), ptr(b), ptr(b_off), ptr(c), ptr(c_off), pm.P_DEFAULT, pm.PM_PLAIN, 0, 6, NULL) == 1
+    assert f(1, ptr(a), ptr(a_off), ptr(b), ptr(b_off), ptr(a), ptr(c_off), pm.P_DEFAULT, pm.PM_PLAIN, 0, 7, NULL) == 1
+    assert f(-1, ptr(a), ptr(a_off), ptr(b), ptr(b_off), ptr(c), ptr(c_off), pm.P_DEFAULT, pm.PM_PLAIN, 0, 7, NULL) == 1
+    assert f(0, ptr(a), ptr(a_off), ptr(b), ptr(b_off), ptr(c), ptr(c_off), pm.P_DEFAULT, pm.PM_PLAIN, 0, 7, NULL) == 0
+    big = 1 << 25                                              # tensor form: max_deg beyond its range
+    assert f(1, ptr(a), ptr(a_off), ptr(b), ptr(b_off), ptr(c), ptr(c_off), pm.P_DEFAULT, pm.PM_TENSOR, 0, big, NULL) != 0
+
+
 def test_status_strings(lib):
     for code in range(8):
         assert lib.polymul_status_string(code)
