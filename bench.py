@@ -614,12 +614,18 @@ def measure_rows(pm, torch, dev, flush, clocks, pk, args):
                        out=outb, total=outb.numel(), stream=gs)
     ms_g = median_ms(g.replay, 20, flush, stream)
     want = outb.clone()  # the graph replay's result; the forms below must agree with it
-    # the tensor-core form on the same batch (what PM_AUTO picks for degrees above 2048)
+    # the tensor-core form on the whole batch
     run_bt = lambda: pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_TENSOR, out=outb,
                                 total=outb.numel())
     run_bt()
     ms_bt = median_ms(run_bt, 10, flush, stream)
     assert torch.equal(outb, want), "batched: tensor and plain forms disagree"
+    # PM_AUTO: each pair by its size (shorter operand of 128 terms or more to the tensor cores)
+    run_ba = lambda: pm.batched(ta[0], ta[1], ta[2], ta[3], ta[4], max_deg=2048, mode=pm.PM_AUTO, out=outb,
+                                total=outb.numel())
+    run_ba()
+    ms_ba = median_ms(run_ba, 20, flush, stream)
+    assert torch.equal(outb, want), "batched: PM_AUTO and the plain form disagree"
     rows["batched_plain"] = {"workload": "4096 pairs, degrees log-uniform in [16,2048]", "s": s_b, "q": q_b,
                              "form": "warp-level units (degrees below 4096)",
                              "tuner": "polymul_tune_batched: flushed medians of 10 calls per (s, Q)",
@@ -627,6 +633,9 @@ def measure_rows(pm, torch, dev, flush, clocks, pk, args):
                                         "model_T_thm_s": model_b.get(sv)}
                                        for (sv, qv), ms_ in sorted(tune_b.items())],
                              "tensor_form_ms_same_batch": ms_bt,
+                             "auto_ms_same_batch": ms_ba, "auto_macs_per_s": macs / (ms_ba * 1e-3),
+                             "auto_form": "PM_AUTO: pairs whose shorter operand has >= 128 terms on the tensor "
+                                          "cores, the others on the warp-level plain form",
                              "macs": macs, "ms_graph": ms_g, "ms_direct": ms_direct,
                              "macs_per_s": macs / (ms_g * 1e-3), "products_per_s": 4096 / (ms_g * 1e-3),
                              "alu_frac": macs / (ms_g * 1e-3) / alu_peak}

@@ -58,7 +58,7 @@ typedef enum {
 } pm_status;
 
 /* Modes of polymul_batched. */
-#define PM_AUTO 0    /* tensor-core form where it applies, else the plain form */
+#define PM_AUTO 0    /* each pair by its size: tensor cores for the larger, plain for the smaller */
 #define PM_PLAIN 1   /* s-blocked CUDA-core product */
 #define PM_TENSOR 2  /* bf16-limb Toeplitz product on the tcgen05 tensor cores */
 
@@ -174,11 +174,15 @@ pm_status polymul_ntt(const uint32_t *a, int64_t deg_a, const uint32_t *b, int64
  * The warp-level form holds up to 64 MiB of scratch per (device, stream).
  * PM_TENSOR computes the same residues on the tensor cores (bf16 limbs, fp32
  * accumulation that stays exact below 2^24: pairs whose shorter operand has
- * more than 4096 terms are accumulated in groups of at most 4096 terms and
- * the groups' residues added); it needs p < 2^29 and
- * max_deg <= PM_TENSOR_MAX_DEG, else returns PM_ERR_UNSUPPORTED.  PM_AUTO uses
- * it when it applies and max_deg > 2048 (below that the plain form measured
- * faster).
+ * more terms than one accumulation may sum, max_terms of polymul_tensor_limbs,
+ * are accumulated in groups of at most that many terms and the groups'
+ * residues added); it needs p < 2^29 and
+ * max_deg <= PM_TENSOR_MAX_DEG, else returns PM_ERR_UNSUPPORTED.  PM_AUTO,
+ * where the tensor cores apply, sends each pair by its size: pairs whose
+ * shorter operand has at least 128 terms to the tensor cores and the others
+ * to the warp-level plain form (both launched on `stream`, each skipping the
+ * other's pairs), or, when max_deg > 4095 or the plain s is 64, the whole
+ * batch to the tensor cores; where they do not apply, the plain form.
  * With s = 0 the plain form takes the tuned (s, Q) of the batch's size class
  * (polymul_tune_batched), else the tuned s of a single pair of degree max_deg
  * (polymul_tune_plain), else 8 from max_deg 1023 up, 4 from 63, else 2.

@@ -327,26 +327,45 @@ pm_status polymul_batched(int64_t batch, const uint32_t* a_data, const int64_t* 
     // layout is reported by the planners)
     if ((rc = chk_input(a_data, 0, a_off + batch, p, stream, ws)) != PM_OK) return rc;
     if ((rc = chk_input(b_data, 0, b_off + batch, p, stream, ws)) != PM_OK) return rc;
-    // PM_AUTO: the tensor cores for batches with degrees above 2048; below, the
-    // warp-level plain form measured faster (4096 pairs of degrees in [16, 2048]:
-    // 0.19 ms against 0.21 ms)
-    const bool tensor_auto = tensor_ok && max_deg > 2048;
-    if (mode == PM_TENSOR || (mode == PM_AUTO && tensor_auto)) {
-        rc = launch_batched_tensor(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg,
-                                   (cudaStream_t)stream, ws);
-        if (rc != PM_ERR_UNSUPPORTED || mode == PM_TENSOR) return rc;
-    }
     // the tuned (s, Q) of this size class (polymul_tune_batched), else the defaults; an explicit s
     // keeps the tuned Q only if it was tuned with that s
-    int64_t q = 0;
-    TuneChoice tc;
-    if (tune_get(PM_TUNE_BATCHED, p, max_deg + 1, batch, &tc) && tc.s > 0) {
-        if (s == 0) s = tc.s;
-        if (s == tc.s) q = tc.q;
+    auto plain_choice = [&](int* s_out, int64_t* q_out) {
+        int sv = s;
+        int64_t q = 0;
+        TuneChoice tc;
+        if (tune_get(PM_TUNE_BATCHED, p, max_deg + 1, batch, &tc) && tc.s > 0) {
+            if (sv == 0) sv = tc.s;
+            if (sv == tc.s) q = tc.q;
+        }
+        if (sv == 0) sv = default_s(max_deg + 1, max_deg + 1, p);
+        *s_out = sv;
+        *q_out = q;
+    };
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mode == PM_TENSOR)
+        return launch_batched_tensor(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, 0, st, ws);
+    if (mode == PM_AUTO && tensor_ok) {
+        // PM_AUTO: each pair by its size.  Pairs whose shorter operand has at least PM_AUTO_SPLIT
+        // terms go to the tensor cores, the others to the warp-level plain form (both forms plan
+        // the whole batch and skip the other's pairs); batches beyond the warp form's degrees, or
+        // whose plain s rules it out, go to the tensor cores whole.
+        int sv = 0;
+        int64_t q = 0;
+        plain_choice(&sv, &q);
+        if (max_deg <= 4095 && sv <= 32) {
+            rc = launch_batched_tensor(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg,
+                                       PM_AUTO_SPLIT, st, ws);
+            if (rc != PM_OK) return rc;
+            return launch_batched_plain(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, sv, max_deg, q,
+                                        PM_AUTO_SPLIT, st, ws);
+        }
+        return launch_batched_tensor(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, 0, st, ws);
     }
-    if (s == 0) s = default_s(max_deg + 1, max_deg + 1, p);
-    return launch_batched_plain(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, s, max_deg, q,
-                                (cudaStream_t)stream, ws);
+    int sv = 0;
+    int64_t q = 0;
+    plain_choice(&sv, &q);
+    return launch_batched_plain(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, sv, max_deg, q,
+                                PM_ALL_PAIRS, st, ws);
 }
 
 pm_status polymul_model_predict(int64_t n, int64_t m, int s, int ell, double U, double P,
@@ -483,7 +502,7 @@ pm_status polymul_tune_batched(int64_t batch, const uint32_t* a_data, const int6
             const int64_t qv = warp_form ? qcand[j] : 0;
             auto call = [&]() {
                 return launch_batched_plain(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, sv, max_deg, qv,
-                                            st, ws);
+                                            PM_ALL_PAIRS, st, ws);
             };
             rc = median_of(call, reps, flush, flush_bytes, st, e0, e1, ts, &med[i][j]);
         }

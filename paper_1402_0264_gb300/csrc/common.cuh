@@ -203,6 +203,17 @@ inline cudaError_t launch_dep(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 #endif
 }
 
+// Pairs of a batch given to the plain launcher with max_short = PM_ALL_PAIRS are all computed; with a
+// finite max_short only those whose shorter operand has fewer than max_short terms (the others are
+// left to the tensor-core launcher, min_short = max_short).
+constexpr int64_t PM_ALL_PAIRS = INT64_MAX;
+// PM_AUTO's split between the forms: the shorter operand's terms from which a pair goes to the
+// tensor cores (4096 pairs of degrees log-uniform in [16, 2048], ms: split 128 0.162, 256 0.168,
+// 512 0.167, 1024 0.192; the plain form alone 0.184, the tensor form alone 0.191)
+#ifndef PM_AUTO_SPLIT
+#define PM_AUTO_SPLIT 128
+#endif
+
 // Kernel launchers (one translation unit each).
 pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c,
                        uint32_t p, int s, cudaStream_t st, DeviceWorkspace* ws);
@@ -210,12 +221,13 @@ pm_status launch_plain(const uint32_t* a, int64_t n, const uint32_t* b, int64_t 
 pm_status launch_batched_plain(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                const int64_t* c_off, uint32_t p, int s, int64_t max_deg, int64_t q_min,
+                               int64_t max_short,
                                cudaStream_t st, DeviceWorkspace* ws);
 pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m, uint32_t* c,
                      uint32_t p, uint32_t g, cudaStream_t st, DeviceWorkspace* ws);
 pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                 const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
-                                const int64_t* c_off, uint32_t p, int64_t max_deg,
+                                const int64_t* c_off, uint32_t p, int64_t max_deg, int64_t min_short,
                                 cudaStream_t st, DeviceWorkspace* ws);
 pm_status launch_mma_probe(int kind, int64_t iters, double* flops_per_clk_sm, int* exact, cudaStream_t st,
                            DeviceWorkspace* ws);

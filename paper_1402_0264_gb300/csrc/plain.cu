@@ -840,14 +840,17 @@ __device__ __forceinline__ long long block_scan(long long v, long long* sh) {
 __global__ void __launch_bounds__(256) warp_count_kernel(int batch, const int64_t* __restrict__ a_off,
                                                          const int64_t* __restrict__ b_off,
                                                          const int64_t* __restrict__ c_off, int64_t max_deg, int td,
-                                                         int64_t* __restrict__ pos, int64_t* __restrict__ bsum) {
+                                                         int64_t max_short, int64_t* __restrict__ pos,
+                                                         int64_t* __restrict__ bsum) {
     __shared__ long long s_sum[8];
     pdl_trigger();  // the planner may be placed now; it waits for this kernel to end
     const int i = blockIdx.x * 256 + threadIdx.x;
     int64_t np = 0;
     if (i < batch) {
         int64_t n, m;
-        np = pair_dims(i, a_off, b_off, c_off, max_deg, &n, &m) ? pair_positions(n, m, td) : -1;
+        // (a valid pair left to another form, min(n, m) >= max_short, counts no position)
+        np = pair_dims(i, a_off, b_off, c_off, max_deg, &n, &m) ? (min(n, m) < max_short ? pair_positions(n, m, td) : 0)
+                                                                : -1;
         pos[i] = np;
     }
     long long v = np > 0 ? np : 0;
@@ -933,7 +936,8 @@ __global__ void __launch_bounds__(PLAN_THREADS) warp_plan_kernel(int batch, int 
         // (this round overwrites only its own entries)
         np_next = i + PLAN_THREADS < batch ? pl.pos[i + PLAN_THREADS] : 0;
         if (np < 0) s_bad = 1;
-        const int tier = (i >= batch || np < 0) ? 3 : (np > Q ? 0 : (8 * np >= Q ? 1 : 2));
+        // (tier 3: no unit, for a pair past the batch, a bad pair, or one with no position)
+        const int tier = (i >= batch || np <= 0) ? 3 : (np > Q ? 0 : (8 * np >= Q ? 1 : 2));
         const long long nu = tier == 0 ? div_up(np, Q) : 0;
         long long xp = np > 0 ? np : 0, x0 = nu, x1 = tier == 1;
         block_scan3(xp, x0, x1, s_scan);
@@ -1092,7 +1096,7 @@ template <int S>
 static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                        const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                        const int64_t* c_off, uint32_t p, int64_t max_deg, int64_t q_min,
-                                       cudaStream_t st, DeviceWorkspace* ws) {
+                                       int64_t max_short, cudaStream_t st, DeviceWorkspace* ws) {
     using W = WCfg<S>;
     auto kern = plain_warp_kernel<S>;
     static int occ_cache[64] = {};
@@ -1126,7 +1130,7 @@ static pm_status launch_batched_warp_s(int64_t batch, const uint32_t* a_data, co
     e = chk_bind(ws);
     if (e != cudaSuccess) return cuda_fail(e);
     warp_count_kernel<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg,
-                                                                      W::TD, pl.pos, pl.bsum);
+                                                                      W::TD, max_short, pl.pos, pl.bsum);
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = launch_dep(warp_plan_kernel, dim3(1), dim3(PLAN_THREADS), 0, st, (int)batch, (int)W::TD, qm, pl,
@@ -1147,10 +1151,11 @@ template <int S>
 static pm_status launch_batched_s(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                   const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                   const int64_t* c_off, uint32_t p, int64_t max_deg, int64_t q_min,
-                                  cudaStream_t st, DeviceWorkspace* ws) {
+                                  int64_t max_short, cudaStream_t st, DeviceWorkspace* ws) {
     if (max_deg <= WK_MAX_DEG && S <= 32)  // (64 sums per lane would spill in the warp form)
-        return launch_batched_warp_s<S>(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, q_min, st,
-                                        ws);
+        return launch_batched_warp_s<S>(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, q_min,
+                                        max_short, st, ws);
+    if (max_short != PM_ALL_PAIRS) return PM_ERR_UNSUPPORTED;  // the CTA form computes every pair
     using C = Cfg<S>;
     auto kern = plain_sk_kernel<S, true>;
     static int occ_cache[64] = {};
@@ -1186,11 +1191,12 @@ static pm_status launch_batched_s(int64_t batch, const uint32_t* a_data, const i
 pm_status launch_batched_plain(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
                                const int64_t* c_off, uint32_t p, int s, int64_t max_deg, int64_t q_min,
-                               cudaStream_t st, DeviceWorkspace* ws) {
+                               int64_t max_short, cudaStream_t st, DeviceWorkspace* ws) {
     switch (s) {
 #define PM_CASE(SV) \
     case SV:        \
-        return launch_batched_s<SV>(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, q_min, st, ws);
+        return launch_batched_s<SV>(batch, a_data, a_off, b_data, b_off, c_data, c_off, p, max_deg, q_min, max_short, \
+                                    st, ws);
         PM_CASE(1) PM_CASE(2) PM_CASE(4) PM_CASE(8) PM_CASE(16) PM_CASE(32) PM_CASE(64)
 #undef PM_CASE
         default: return PM_ERR_INVALID_ARG;

@@ -736,7 +736,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_batched_kernel(
 __global__ void __launch_bounds__(1024) tc_plan_kernel(int batch, const int64_t* __restrict__ a_off,
                                                         const int64_t* __restrict__ b_off,
                                                         const int64_t* __restrict__ c_off, int64_t max_deg,
-                                                        int64_t* prefix, unsigned long long* counter, int* status) {
+                                                        int64_t min_short, int64_t* prefix,
+                                                        unsigned long long* counter, int* status) {
     __shared__ long long s_scan[1024];
     __shared__ int s_bad;
     pdl_trigger();  // the product kernel may be placed now; it waits for this one to end
@@ -753,7 +754,7 @@ __global__ void __launch_bounds__(1024) tc_plan_kernel(int batch, const int64_t*
             s_bad = 1;
             continue;
         }
-        run += (n + m - 1 + TILE_OUT - 1) / TILE_OUT;
+        run += min(n, m) >= min_short ? (n + m - 1 + TILE_OUT - 1) / TILE_OUT : 0;
     }
     s_scan[tid] = run;
     __syncthreads();
@@ -775,7 +776,7 @@ __global__ void __launch_bounds__(1024) tc_plan_kernel(int batch, const int64_t*
     for (int i = lo; i < hi; ++i) {
         prefix[i] = pos;
         const int64_t n = a_off[i + 1] - a_off[i], m = b_off[i + 1] - b_off[i];
-        pos += (n + m - 1 + TILE_OUT - 1) / TILE_OUT;
+        pos += min(n, m) >= min_short ? (n + m - 1 + TILE_OUT - 1) / TILE_OUT : 0;
     }
     if (tid == 1023) {
         prefix[batch] = s_scan[1023];
@@ -973,8 +974,8 @@ pm_status launch_mma_probe(int kind, int64_t iters, double* flops_per_clk_sm, in
 
 pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int64_t* a_off,
                                 const uint32_t* b_data, const int64_t* b_off, uint32_t* c_data,
-                                const int64_t* c_off, uint32_t p, int64_t max_deg, cudaStream_t st,
-                                DeviceWorkspace* ws) {
+                                const int64_t* c_off, uint32_t p, int64_t max_deg, int64_t min_short,
+                                cudaStream_t st, DeviceWorkspace* ws) {
     if (p >= (1u << 29) || max_deg > TC_MAX_DEG) return PM_ERR_UNSUPPORTED;
     if (ws->cc_major != 10) return PM_ERR_UNSUPPORTED;  // tcgen05 needs the sm_100 family
     StreamScratch* sc = nullptr;
@@ -1005,7 +1006,8 @@ pm_status launch_batched_tensor(int64_t batch, const uint32_t* a_data, const int
     }
     e = chk_bind(ws);
     if (e != cudaSuccess) return cuda_fail(e);
-    tc_plan_kernel<<<1, 1024, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg, prefix, counter, ws->status);
+    tc_plan_kernel<<<1, 1024, 0, st>>>((int)batch, a_off, b_off, c_off, max_deg, min_short, prefix, counter,
+                                       ws->status);
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = launch_dep(tc_batched_kernel, dim3(ws->num_sms), dim3(TC_THREADS), TC_SMEM, st, (int)batch, a_data,
