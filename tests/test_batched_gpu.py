@@ -146,3 +146,24 @@ def test_batched_tuner_records_and_uses_its_choice(tmp_path):
         assert pm.tune_lookup(*key) == (best_s, q)
         assert_equal(run_batch(packed, 2048, s=0), want, f"Q = {q}")
     pm.tune_clear()
+
+
+@pytest.mark.parametrize("kind", ["all_small", "all_large", "mixed", "at_the_split"])
+def test_auto_splits_pairs_by_size(kind):
+    """PM_AUTO sends pairs whose shorter operand has at least 128 terms to the tensor cores and the
+    others to the warp-level plain form, each form's planner skipping the other's pairs: batches
+    with only small pairs, only large ones, both, and pairs at the boundary (127 and 128 terms) all
+    match the oracle word for word."""
+    rng = np.random.default_rng(1404)
+    if kind == "all_small":
+        da = rng.integers(0, 127, 40); db = rng.integers(0, 2000, 40)
+    elif kind == "all_large":
+        da = rng.integers(127, 2048, 40); db = rng.integers(127, 2048, 40)
+    elif kind == "mixed":
+        da = rng.integers(0, 2048, 80); db = rng.integers(0, 2048, 80)
+    else:
+        da = np.array([126, 127, 128, 127, 2047, 127, 0, 127]); db = np.array([127, 127, 127, 2047, 127, 126, 2047, 128])
+    packed = inputs.packed_batch(da.astype(np.int64), db.astype(np.int64), 1405 + len(kind))
+    want = oracle.polymul_batch(*packed[:4], packed[4], P)
+    assert_equal(run_batch(packed, 2047, mode=pm.PM_AUTO), want, kind)
+    assert_equal(run_batch(packed, 2047, mode=pm.PM_AUTO), want, kind + " again")
