@@ -92,8 +92,11 @@ static_assert(NBLK % 16 == 0 && MMA_N <= 256, "tile width");
 constexpr int TILE_OUT = TT * NBLK;        // 2048 (or 1536)
 constexpr int TC_GROUP = TC_MAXK / TT;     // shifts per K-group when both operands are longer
 constexpr int64_t TC_MAX_DEG = PM_TENSOR_MAX_DEG;      // degrees this path takes (int tile indices)
-constexpr int GROUP_D = 8;                 // shifts per Hankel slot
-constexpr int NH = 4;                      // Hankel slots in the ring
+constexpr int GROUP_D = 24;                // shifts per Hankel slot
+constexpr int NH = 2;                      // Hankel slots in the ring
+// (1024 pairs of degree 4095 / 64 of degree 16383, ms: 4 slots of 8 shifts 0.457 / 0.390, 6 of 8
+// 0.461 / 0.394, 3 of 8 0.459 / 0.394, 2 of 16 0.431 / 0.365, 3 of 16 0.433 / 0.367, 2 of 24
+// 0.425 / 0.369: fewer, larger slots mean fewer hand-overs between the builders and the MMAs)
 constexpr int MAX_DELTA = TC_MAXK / TT + 2;            // shifts a tile can need
 constexpr int BD_SHIFT = 7;                            // staged b digit t sits at index t + 7
 constexpr int BD_LEN = TT * (MAX_DELTA + 2);           // b digits staged per limb (with the shift)
@@ -132,11 +135,11 @@ constexpr int TC_SMEM = SM_CTL + 576;
 constexpr int BAR_A_FULL = 0;       // [2] tile record + a operand staged (stager leader)
 constexpr int BAR_STAGE_EMPTY = 2;  // [2] MMAs of the tile that used the a operand done (commit)
 constexpr int BAR_H_FULL = 4;       // [NH] Hankel slot built (builder leader)
-constexpr int BAR_H_EMPTY = 8;      // [NH] MMAs reading the slot done (commit)
-constexpr int BAR_ACC_FULL = 12;    // [2] accumulator complete: record written + MMAs done (2 arrivals)
-constexpr int BAR_ACC_EMPTY = 14;   // [2] accumulator read back (one arrival per epilogue warp)
-constexpr int BAR_DRAIN = 16;       // all MMAs issued by the CTA done
-constexpr int NUM_BARS = 17;
+constexpr int BAR_H_EMPTY = BAR_H_FULL + NH;      // [NH] MMAs reading the slot done (commit)
+constexpr int BAR_ACC_FULL = BAR_H_EMPTY + NH;    // [2] accumulator complete: record written + MMAs done (2 arrivals)
+constexpr int BAR_ACC_EMPTY = BAR_ACC_FULL + 2;   // [2] accumulator read back (one arrival per epilogue warp)
+constexpr int BAR_DRAIN = BAR_ACC_EMPTY + 2;       // all MMAs issued by the CTA done
+constexpr int NUM_BARS = BAR_DRAIN + 1;
 static_assert(NUM_BARS * 8 <= CTL_TILES, "control block");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
