@@ -484,7 +484,8 @@ __device__ __forceinline__ uint2 root_pair(uint32_t e, const uint2* lo, const ui
     return make_uint2(w, (uint32_t)(((uint64_t)w << 32) / p));
 }
 
-// ---- N <= 4096: one CTA per product ----
+// ---- N < 1024, or N <= 4096 with a prime of 2-adic order below 12: one CTA, length-N transforms in
+// shared memory ----
 __global__ void __launch_bounds__(NTT_THREADS) ntt_small_kernel(
     const uint32_t* __restrict__ a, int n, const uint32_t* __restrict__ b, int m,
     uint32_t* __restrict__ c, int logn, NttTables tb, NttMod md) {
@@ -550,32 +551,15 @@ __global__ void __launch_bounds__(NTT_THREADS, NTT_COL_MINB) ntt_col_fwd_kernel(
     }
 }
 
-// ---- four-step pass 2: per row, forward row transforms, product, inverse ----
-__global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __restrict__ ta,
-                                                      const uint32_t* __restrict__ tbuf,
-                                                      int logn1, NttTables tb, NttMod md) {
-    __shared__ uint32_t sA[ROW_WORDS];
-    __shared__ uint32_t sB[ROW_WORDS];
+// The product of one row pair in registers (the pass-2 work of a row): on entry thread t holds
+// elements t + 256 l (l < 16) of the two length-4096 rows in r and q, on exit the inverse
+// transform of their transforms' pointwise product (Montgomery: times 2^-32) in r, in the same
+// positions; sA and sB are the CTA's exchange arrays.
+__device__ __forceinline__ void row_product(uint32_t (&r)[16], uint32_t (&q)[16], uint32_t* sA, uint32_t* sB,
+                                            const NttTables& tb, const NttMod& md) {
     const int t = threadIdx.x;
-    const size_t r0 = (size_t)blockIdx.x * NTT_N2;
-    pdl_wait();  // the column pass's transforms
-    pdl_trigger();
-    if (!PM_CHK(blockIdx.x < (1u << logn1) && blockDim.x == 256)) return;  // (uniform: before any barrier)
     const uint32_t p = md.p;
     const uint2 w4 = tb.rw4, iw4 = tb.riw4;
-    const uint32_t k1 = freq_of_pos_fast(blockIdx.x, logn1);
-    const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
-    // the final twist by w_N^-(i k1), i = t + 256 l, as w_N^-(256 l k1) (one per l, for the whole
-    // CTA: sC, read after the barriers below) times w_N^-(t k1) (one per thread)
-    __shared__ uint2 sC[16];
-    if (t < 16) sC[t] = root_pair((uint32_t)((256ull * t * k1) & nmask), tb.ilo, tb.ihi, p);
-    uint32_t r[16], q[16];
-    // stage 1 of both rows, straight from global memory
-#pragma unroll
-    for (int l = 0; l < 16; ++l) {
-        r[l] = ta[r0 + t + 256 * l];
-        q[l] = tbuf[r0 + t + 256 * l];
-    }
     uint32_t (*rq[2])[16] = {&r, &q};
     uint32_t (*ro[1])[16] = {&r};
     row_stage_n<true, 2>(1, rq, w4, tb.row, tb.st3, p);
@@ -621,9 +605,63 @@ __global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __
 #pragma unroll
     for (int l = 0; l < 16; ++l) r[l] = sA[rphys(t + 256 * l)];
     row_stage_n<false, 1>(1, ro, iw4, tb.irow, tb.ist3, p);
+}
+
+// ---- four-step pass 2: per row, forward row transforms, product, inverse ----
+__global__ void __launch_bounds__(256, NTT_ROW_MINB) ntt_row_kernel(uint32_t* __restrict__ ta,
+                                                      const uint32_t* __restrict__ tbuf,
+                                                      int logn1, NttTables tb, NttMod md) {
+    __shared__ uint32_t sA[ROW_WORDS];
+    __shared__ uint32_t sB[ROW_WORDS];
+    const int t = threadIdx.x;
+    const size_t r0 = (size_t)blockIdx.x * NTT_N2;
+    pdl_wait();  // the column pass's transforms
+    pdl_trigger();
+    if (!PM_CHK(blockIdx.x < (1u << logn1) && blockDim.x == 256)) return;  // (uniform: before any barrier)
+    const uint32_t p = md.p;
+    const uint32_t k1 = freq_of_pos_fast(blockIdx.x, logn1);
+    const uint64_t nmask = ((((uint64_t)1) << logn1) << NTT_N2_LOG) - 1;
+    // the final twist by w_N^-(i k1), i = t + 256 l, as w_N^-(256 l k1) (one per l, for the whole
+    // CTA: sC, read after the barriers below) times w_N^-(t k1) (one per thread)
+    __shared__ uint2 sC[16];
+    if (t < 16) sC[t] = root_pair((uint32_t)((256ull * t * k1) & nmask), tb.ilo, tb.ihi, p);
+    uint32_t r[16], q[16];
+    // stage 1 of both rows, straight from global memory
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        r[l] = ta[r0 + t + 256 * l];
+        q[l] = tbuf[r0 + t + 256 * l];
+    }
+    row_product(r, q, sA, sB, tb, md);
     const uint2 bt = root_pair((uint32_t)(((uint64_t)t * k1) & nmask), tb.ilo, tb.ihi, p);
 #pragma unroll
     for (int l = 0; l < 16; ++l) ta[r0 + t + 256 * l] = mul_shoup_lz(mul_shoup_lz(r[l], sC[l], p), bt, p);
+}
+
+// ---- products with N <= 4096: one row pair in one CTA ----
+// The length-4096 transform of the row pass, on a and b zero-padded to 4096 words (a cyclic product
+// of length 4096 is the whole product when n + m - 1 <= 4096), then the scale N^-1 2^32 and the
+// store of the n + m - 1 output words.
+__global__ void __launch_bounds__(256) ntt_one_row_kernel(const uint32_t* __restrict__ a, int n,
+                                                          const uint32_t* __restrict__ b, int m,
+                                                          uint32_t* __restrict__ c, int L, NttTables tb, NttMod md) {
+    __shared__ uint32_t sA[ROW_WORDS];
+    __shared__ uint32_t sB[ROW_WORDS];
+    const int t = threadIdx.x;
+    if (!PM_CHK(blockDim.x == 256 && n + m - 1 <= NTT_N2)) return;  // (uniform: before any barrier)
+    uint32_t r[16], q[16];
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        const int i = t + 256 * l;
+        r[l] = i < n ? a[i] : 0u;
+        q[l] = i < m ? b[i] : 0u;
+    }
+    row_product(r, q, sA, sB, tb, md);
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        const int i = t + 256 * l;
+        if (i < L) c[i] = mul_shoup(r[l], tb.scale, md.p);
+    }
 }
 
 // ---- four-step pass 3: inverse column transforms, scale, store ----
@@ -725,7 +763,7 @@ static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStrea
         lo[e] = shoup_pair(powmod_h(w, (uint64_t)e % N, p), p);
         ilo[e] = shoup_pair(powmod_h(wi, (uint64_t)e % N, p), p);
     }
-    if (logn > NTT_N2_LOG) {  // the row transforms' twiddles in thread order (RT_A1 ...)
+    if (logn >= NTT_N2_LOG) {  // the row transforms' twiddles in thread order (RT_A1 ...)
         const uint32_t w2 = powmod_h(w, (uint64_t)n1, p), w2i = powmod_h(wi, (uint64_t)n1, p);  // w_N2, w_N2^-1
         auto fill = [&](uint2* T, uint32_t base) {
             auto pw = [&](uint64_t x) { return shoup_pair(powmod_h(base, x % NTT_N2, p), p); };
@@ -766,7 +804,7 @@ static pm_status get_tables(int dev, uint32_t p, uint32_t g, int logn, cudaStrea
     const uint32_t ninv = powmod_h(N % p, p - 2, p);
     const uint32_t r32 = (uint32_t)((1ull << 32) % p);
     ts.t.scale = shoup_pair((uint32_t)((uint64_t)ninv * r32 % p), p);
-    if (logn > NTT_N2_LOG) {
+    if (logn >= NTT_N2_LOG) {
         const uint32_t w2 = powmod_h(w, (uint64_t)n1, p), w2i = powmod_h(wi, (uint64_t)n1, p);  // w_N2, w_N2^-1
         for (int l0 = 1; l0 <= 3; ++l0)
             for (int k = 1; k <= 3; ++k) {
@@ -800,8 +838,13 @@ pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m,
     if (logn > NTT_MAX_LOG) return PM_ERR_RANGE;
     if (logn < 2) logn = 2;
     if ((uint64_t)(p - 1) % (1ull << logn) != 0) return PM_ERR_UNSUPPORTED;
+    // 1024 <= N <= 4096 takes the length-4096 row transform when p allows it (4096 | p - 1): one
+    // CTA, 12.9 us on GB300 at every such N, where the length-N transform in shared memory took
+    // 19 us (N = 2048) and 31 us (N = 4096); below 1024 points the latter is faster (8.9 us at
+    // N = 32, 10.9 us at N = 512) and keeps them, as it keeps primes of 2-adic order below 12
+    const bool one_row = logn >= 10 && logn <= NTT_N2_LOG && (p - 1) % NTT_N2 == 0;
     NttTables tb;
-    pm_status rc = get_tables(ws->device, p, g, logn, st, &tb);
+    pm_status rc = get_tables(ws->device, p, g, one_row ? NTT_N2_LOG : logn, st, &tb);
     if (rc != PM_OK) return rc;
     cudaError_t eb = chk_bind(ws);
     if (eb != cudaSuccess) return cuda_fail(eb);
@@ -811,6 +854,13 @@ pm_status launch_ntt(const uint32_t* a, int64_t n, const uint32_t* b, int64_t m,
     for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
     md.pinv_neg = 0u - inv;
     cudaError_t e;
+    if (one_row) {
+        ntt_one_row_kernel<<<1, 256, 0, st>>>(a, (int)n, b, (int)m, c, (int)L, tb, md);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e);
+        count_launches(1);
+        return PM_OK;
+    }
     if (logn <= NTT_N2_LOG) {
         const size_t smem = 2 * sizeof(uint32_t) * ((size_t)1 << logn);
         static int done[64] = {};

@@ -79,6 +79,21 @@ def test_other_prime_with_generator():
     assert_equal(run(a, b, p=p, g=g), oracle.ntt_polymul(a, b, p, g), "p=998244353")
 
 
+@pytest.mark.parametrize("p,g", [(7681, 17), (12289, 11)])
+def test_small_products_with_primes_of_low_two_adic_order(p, g):
+    """7681 = 15 * 2^9 + 1 admits transforms up to length 512 only (the length-N transform in
+    shared memory); 12289 = 3 * 2^12 + 1 exactly the length-4096 row transform, which products of
+    1024 to 4096 points take."""
+    top = (p - 1) & -(p - 1)
+    for n, m in [(1, 1), (100, 29), (top // 2, top // 2), (top - 5, 6), (3, top - 2)]:
+        a = inputs.uniform_mod(60 + n, 1, n, p)
+        b = inputs.uniform_mod(60 + m, 2, m, p)
+        assert_equal(run(a, b, p=p, g=g), oracle.polymul(a, b, p), f"p={p} {n}x{m}")
+    with pytest.raises(pm.PolymulError) as e:
+        pm.ntt(dev(np.ones(top, np.uint32)), dev(np.ones(2, np.uint32)), p=p, g=g)
+    assert e.value.code == 3                # the product needs a transform of length 2 top
+
+
 def test_unsupported_cases():
     a = dev(np.ones(70000, np.uint32))
     with pytest.raises(pm.PolymulError) as e:
