@@ -45,8 +45,10 @@
 
 namespace pm {
 
-constexpr int GCD_THREADS = 512;               // 16 warps: latency hiding for the replay
-constexpr int GCD_T = 256;                     // output positions per block
+// (degrees 9999 and 8999, s = 64, ms: 256 positions and 512 threads per block 9.51, 128 and 512
+// 9.37, 64 and 512 10.02, 256 and 256 10.52, 128 and 256 9.19, 64 and 256 9.32, 128 and 128 10.58)
+constexpr int GCD_THREADS = 256;               // 8 warps
+constexpr int GCD_T = 128;                     // output positions per block
 constexpr int GCD_SMAX = 256;                  // largest s
 constexpr int GCD_HEXTRA = 32;                 // head length H = s + GCD_HEXTRA
 constexpr int GCD_HMAX = GCD_SMAX + GCD_HEXTRA;
