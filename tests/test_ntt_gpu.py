@@ -27,7 +27,7 @@ def run(a, b, p=P, g=0):
 
 
 SHAPES = [(1, 1), (2, 1), (3, 3), (100, 29), (1024, 1024), (2048, 2049), (2049, 2048),
-          (5000, 3000), (4097, 1), (20000, 12289), (65537, 3)]
+          (5000, 3000), (4097, 1), (8192, 1), (4096, 4096), (6000, 2193), (20000, 12289), (65537, 3)]
 
 
 @pytest.mark.parametrize("n,m", SHAPES)
@@ -77,6 +77,10 @@ def test_other_prime_with_generator():
     a = inputs.uniform_mod(5, 1, 70000, p)
     b = inputs.uniform_mod(5, 2, 50000, p)
     assert_equal(run(a, b, p=p, g=g), oracle.ntt_polymul(a, b, p, g), "p=998244353")
+    for n, m in [(5000, 3000), (2000, 2000), (100, 29)]:  # transforms of 8192, 4096 and 128 points
+        a = inputs.uniform_mod(6, 1, n, p)
+        b = inputs.uniform_mod(6, 2, m, p)
+        assert_equal(run(a, b, p=p, g=g), oracle.polymul(a, b, p), f"p=998244353 {n}x{m}")
 
 
 @pytest.mark.parametrize("p,g", [(7681, 17), (12289, 11)])
