@@ -24,11 +24,14 @@
 // elements per thread, two radix-4 levels per stage) with two shared-memory
 // exchanges, and the pointwise product sits between the last forward and the
 // first inverse stage without leaving registers.  N <= 4096 runs in one CTA
-// per product.
+// per product: from 1024 points on, the row pass's length-4096 transform on a
+// and b zero-padded to 4096 words; below that (and for primes whose 2-adic
+// order is below 12) length-N transforms level by level in shared memory.
 //
-// Arithmetic: the four-step passes keep values in [0, 2p) between butterflies
-// (the lazy forms below; 4p < 2^32 since p < 2^30) and the inverse column pass's
-// final scale makes them canonical; the one-CTA path keeps them in [0, p).
+// Arithmetic: the four-step passes and the one-CTA row transform keep values
+// in [0, 2p) between butterflies (the lazy forms below; 4p < 2^32 since
+// p < 2^30) and the final scale makes them canonical; the level-by-level
+// shared-memory path keeps them in [0, p).
 // Multiplication by a table
 // constant w uses Shoup's precomputed quotient wq = floor(w 2^32 / p)
 // (V. Shoup, NTL; also D. Harvey, "Faster arithmetic for number-theoretic
