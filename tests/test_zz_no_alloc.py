@@ -6,7 +6,8 @@ gives every allocation to one owner).  Its scratch lives in a static device
 array.
 
 Checked here through the C ABI: two calls in a row give exactly the words
-that polymul_plain gives (for several s and both operand orders), and after
+that polymul_plain gives, which are the CPU oracle's (for several s and both
+operand orders), and after
 the first call (which sets the array up) the calls leave the device's free
 memory unchanged.  This file is collected last so that a run stopping at the
 first failure has run every other test.
@@ -16,6 +17,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_1402_0264_gb300 import inputs
 from paper_1402_0264_gb300 import polymul as pm
 from tests.gpuhelp import assert_equal, dev, host
@@ -54,6 +56,8 @@ def test_noalloc_matches_plain_on_two_calls_in_a_row():
     # the references also load every kernel instance used below and the fill kernel before
     # the free-memory baseline: lazy module loading takes device memory on first use
     refs = [host(pm.plain(a, b, s=s)) for (a, b), s in zip(tensors, svals)]
+    for (a, b, s), ref in zip(cases, refs):
+        assert_equal(ref, oracle.polymul(a, b, P), f"reference s={s} against the oracle")
     for out in outs:
         out.fill_(0)
     # first call on this device: sets the static array up
