@@ -1,7 +1,8 @@
 """The bench's model ratios for division (Section 3) and the gcd (Section 6) against the closed
 forms the paper prints for them.  The paper substitutes l = Z/2 and s = Z/7 (division), and
 l = Z/2, s = Z/6, m = n (gcd); under those substitutions the ratios T_1/T_s built from its N, L
-and C must reduce to the printed R.  Host arithmetic only."""
+and C must reduce to the printed R.  Also the bench's count of the tensor kernel's issued work,
+against a brute-force enumeration of the shifts each tile meets.  Host arithmetic only."""
 import importlib.util
 import os
 import sys
@@ -59,3 +60,46 @@ def test_gcd_ratio_limit_and_threshold(bench):
         limit = (3 + 5 * U) * Z / (3 * (Z + 16 * U))
         assert bench.gcd_model_ratio(10**12, 10**12, Z / 6, Z / 2, U) == pytest.approx(limit, rel=1e-9)
     assert (3 + 5 * U) * 9.6 / (3 * (9.6 + 16 * U)) == pytest.approx(1.0, rel=1e-12)
+
+
+def _issued_shifts_by_enumeration(n, m, W):
+    """Shifts the tensor kernel issues for one pair, by brute force: for every tile of W output
+    blocks, every shift delta whose b digits (indices 32 delta - 31 .. 32 delta + 31) meet b and
+    whose a block I - delta exists for some output block I of the tile."""
+    if m > n:
+        n, m = m, n
+    na = (n + 31) // 32
+    L = n + m - 1
+    total = 0
+    for I0 in range(0, (L + 31) // 32, W):
+        for delta in range(-2, (m + 31) // 32 + 2):
+            meets_b = 32 * delta - 31 <= m - 1 and 32 * delta + 31 >= 0
+            meets_a = any(0 <= I - delta < na for I in range(I0, I0 + W))
+            total += meets_b and meets_a
+    return total
+
+
+def test_tc_issued_flops_matches_enumeration(bench):
+    import numpy as np
+    enc = {"tile_blocks": 64, "na": 4}
+    rng = np.random.default_rng(5)
+    n = rng.integers(1, 9000, 40)
+    m = rng.integers(1, 9000, 40)
+    n[:4] = [1, 4096, 31, 2593]
+    m[:4] = [1, 4096, 4097, 33]
+    a_off = np.concatenate([[0], np.cumsum(n)])
+    b_off = np.concatenate([[0], np.cumsum(m)])
+    shifts = sum(_issued_shifts_by_enumeration(int(x), int(y), 64) for x, y in zip(n, m))
+    per_shift = 2 * 2 * 128 * 16 * 64 * 4   # two MMAs of 128 x 256 x 16
+    assert bench.tc_issued_flops(a_off, b_off, enc) == shifts * per_shift
+
+
+def test_headline_useful_over_issued_is_two_thirds(bench):
+    """1024 pairs of degree 4095 with 64-block tiles: 384 shifts per pair of 128 x 128 blocks, so
+    the useful share of the issued products is 128 * 128 * 32 / (384 * 64 * 32) = 2/3."""
+    import numpy as np
+    enc = {"tile_blocks": 64, "na": 4}
+    off = np.arange(0, 1025 * 4096, 4096, dtype=np.int64)
+    issued = bench.tc_issued_flops(off, off, enc)
+    useful = 1024 * 4096 * 4096 * 16 * 2
+    assert useful / issued == pytest.approx(2 / 3, rel=1e-12)
